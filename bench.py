@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: CHHS cell-steps/s of the per-step FAS solve at residual 1e-10.
+
+A benchmark step is one time step of the 512 x 512 spinodal workload (2D,
+(0,12.8)^2, eps 0.05, gamma 1, dt 0.005, seeded noise of amplitude 0.05
+about mean 0): one full FAS solve of Eqs. 2.5-2.7 to the 1e-10 stopping norm,
+run through the C ABI.  A cell-step is one cell advanced one time step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One process per GPU (torchrun for N > 1); every rank runs its own replica of
+the workload (runs are independent, so the path shards only across runs),
+the time is the maximum over ranks and `value` counts the cell-steps of all
+ranks.  Rank 0 prints one JSON line.
+
+`--impl reference` times the CPU oracle (the plain double-precision
+lexicographic FAS of ``oracle/``) on the host cores instead, on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CHHS cell-steps/s at 1e-10 residual, mixed vs FP64 form; served p50/p99"
+UNIT = "cell-steps/s"
+WORKLOAD = "spinodal512"
+WORKLOAD_DESC = ("2D spinodal 512x512 on (0,12.8)^2, Neumann, eps=0.05, gamma=1, dt=0.005, "
+                 "phi0 = 0.05*U(-1,1) (SplitMix64 seed 2), FAS V(2,2) to residual 1e-10, FP64")
+L2_FLUSH_BYTES = 256 << 20
+# Nominal FP64 peak of a GB300: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM
+# (2 DFMA per clock per SM) = 1.2586 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# Algorithmic FP64 flops of one smoother cell update (interior cell), counted
+# from the update formula: add/sub/mul/div = 1, fma = 2.  Per face: A_h phi*
+# (2), M = 1 + gamma a^2 (3), the mu and p differences (2), the three flux
+# sums M dmu, a dp, a dmu (6), the phi difference and its sum (2), the sums of
+# dp, M and a (3) = 18.  Per cell: N1 (4), N2 with chi (10), N3 (3), the three
+# residuals (3), 1/n_c (1), Ae (6), C/Dn (2), G (2), B with chi_a (10), the 2x2
+# solve for dphi (7), dmu (2), dp (4), the three updates (3) = 57.
+SMOOTH_FLOPS = {2: 4 * 18 + 57, 3: 6 * 18 + 57}
+KERNEL_SRC = os.path.join(ROOT, "paper_1611_02967_gb300", "csrc", "chhs_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_smooth_spinodal512.txt")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def config(world):
+    return {"workload": WORKLOAD_DESC, "cells": 512 * 512, "workload_steps": 200,
+            "l2": "flushed between timed steps (256 MiB device write, untimed)",
+            "parallelism": "replicas x%d (one independent run per GPU)" % world}
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per k_smooth launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    try:
+        vals = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t0 = time.time()
+        while not self.rows and time.time() - t0 < 5.0:
+            time.sleep(0.05)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(w, max_seconds=15.0, max_steps=40, skip_first=True):
+    """The CPU oracle as it stands, single-threaded, on the first steps of the
+    workload: returns (cell-steps/s, steps timed, seconds)."""
+    import numpy as np
+
+    import oracle
+    prm = oracle.Params(w["h"], w["eps"], w["gamma"], w["dt"], tol=1e-10)
+    phim = np.array(w["phi0"], dtype=np.float64)
+    phimm1 = phim.copy()
+    mu = np.zeros_like(phim)
+    p = np.zeros_like(phim)
+    n = phim.size
+    timed, t_total, k = 0, 0.0, 0
+    while k < max_steps:
+        t0 = time.perf_counter()
+        phi, mu, p, v, r, st = oracle.step(phim, phimm1, prm, 2.0 * phim - phimm1, mu, p)
+        dt = time.perf_counter() - t0
+        if st != oracle.OK:
+            raise RuntimeError("oracle step failed: %d" % st)
+        phimm1, phim = phim, phi
+        if k > 0 or not skip_first:
+            timed += 1
+            t_total += dt
+        k += 1
+        if t_total >= max_seconds:
+            break
+    return n * timed / t_total, timed, t_total
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1611_02967_gb300 import inputs
+    w = inputs.workload(WORKLOAD)
+    n = 512 * 512
+    import numpy as np
+
+    import oracle
+    prm = oracle.Params(w["h"], w["eps"], w["gamma"], w["dt"], tol=1e-10)
+    phim = np.array(w["phi0"])
+    phimm1 = phim.copy()
+    mu = np.zeros_like(phim)
+    p = np.zeros_like(phim)
+    times, vs = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        phi, mu, p, v, r, st = oracle.step(phim, phimm1, prm, 2.0 * phim - phimm1, mu, p)
+        t = time.perf_counter() - t0
+        if st != oracle.OK:
+            raise RuntimeError("oracle step %d failed: %d" % (k, st))
+        phimm1, phim = phim, phi
+        if k >= args.warmup:
+            times.append(t)
+            vs.append(v)
+    total = sum(times)
+    value = n * len(times) / total
+    sample = "time steps %d..%d of the 512x512 workload, one oracle process" % (
+        args.warmup + 1, args.warmup + args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(1),
+            "vcycles_per_step": sum(vs) / len(vs),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def reduce_max(value, world):
+    """Max of a float over ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1611_02967_gb300 import chhs, inputs
+    w = inputs.workload(WORKLOAD)
+    shape, ncell = w["shape"], 512 * 512
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    run = chhs.Run(shape, w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream)
+    run.set_phi(w["phi0"])
+    per_v, per_step = run.launch_counts()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    # warm-up (untimed)
+    run.step(args.warmup)
+    # timed region: K steps, L2 flushed before each, device time by events
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    vtot = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        ev0[k].record(stream)
+        run.step_async(1)
+        ev1[k].record(stream)
+        _, v, resid = run.wait()
+        vtot += v
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    max_ms = reduce_max(dev_ms, world)
+    units = reduce_sum(float(ncell * args.steps), world)
+    value = units / (max_ms / 1e3)
+    launches = args.steps * (per_step + 1) + vtot * per_v
+
+    # end to end through the public API with host-resident state: every step
+    # copies (phi^m, phi^{m-1}, mu, p) in from pinned host memory, solves, and
+    # copies them back out
+    host = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
+    st = run.get_state()
+    for h_, s_ in zip(host, st):
+        h_[...] = s_
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        run.set_state(*host)
+        run.step(1)
+        chhs.lib().chhs_get_state(run.handle, *[chhs._buf(h_, ncell, True)[0] for h_ in host], 0)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e = {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * ncell,
+           "d2h_bytes_per_step": 4 * 8 * ncell}
+
+    # roofline of the dominant kernel: the same steps launched kernel by
+    # kernel with CUDA events on the solver's stream
+    prof = None
+    for _ in range(5):
+        prof = run.profile_step(prof)
+    total_ms = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    sm_ms, sm_launch, sm_units = prof["smooth"]
+    flops = sm_units * SMOOTH_FLOPS[2]
+    achieved = flops / (sm_ms / 1e3) / 1e12
+    traffic = measured_traffic()
+    roofline = {"bound": "alu", "kernel": "k_smooth<double,2> (FP64 red-black cell update)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal FP64 152 SMs x 2.07 GHz x 4 flop/clk (recipe's unit counts)",
+                "traffic": traffic, "dominant_kernel_share": prof["smooth"][0] / total_ms,
+                "avg_launch_us": 1e3 * sm_ms / sm_launch,
+                "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in prof.items()}}
+    if dom != "smooth":
+        roofline["note"] = "largest device-time share this run: %s" % dom
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, nsteps, secs = oracle_rate(w)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "time steps 2..%d of the same 512x512 workload (%.1f s), single-threaded" % (
+                   nsteps + 1, secs)}
+    run.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config(world), "vcycles_per_step": vtot / args.steps, "final_resid": resid,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

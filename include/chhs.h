@@ -1,0 +1,163 @@
+/*
+ * chhs.h -- C ABI of the GB300 (sm_103a) FAS multigrid solver for the
+ * second-order convex-splitting Cahn-Hilliard-Hele-Shaw scheme of
+ * Chen, Feng, Liu, Wang and Wise (arXiv:1611.02967).
+ *
+ * The problem (Section 2, first paragraph, and Eqs. 2.4-2.7): on the box
+ * (0, n_x h) x (0, n_y h) [x (0, n_z h)] with cell-centred grid functions and
+ * homogeneous Neumann boundaries (Appendix A.1), given (phi^{m-1}, phi^m),
+ * find (phi^{m+1}, mu^{m+1/2}, p^{m+1/2}) with
+ *   phi^{m+1} - phi^m = s div_h(M(A_h phi*) grad_h mu) + s div_h(A_h phi* grad_h p)
+ *   mu = chi(phi^{m+1}, phi^m) - phi* - eps^2 Lap_h(3/4 phi^{m+1} + 1/4 phi^{m-1})
+ *   Lap_h p = -gamma div_h(A_h phi* grad_h mu)
+ * with phi* = 3/2 phi^m - 1/2 phi^{m-1}, chi(a,b) = (a^2+b^2)(a+b)/4 and
+ * M(x) = 1 + gamma x^2.  Each step is solved by FAS nonlinear multigrid
+ * V(nu1, nu2)-cycles to a residual tolerance (Section 5 preamble).
+ *
+ * Conventions for every call:
+ *  - Arrays hold interior cells only, x fastest, then y, then z
+ *    (element (i,j,k) at i + n_x (j + n_y k)); doubles.
+ *  - `on_device` = 0: the pointer is host memory (pageable or pinned) and the
+ *    call copies synchronously.  `on_device` = 1: the pointer is device memory
+ *    of the handle's device, read or written in stream order on the handle's
+ *    stream.
+ *  - The caller owns every buffer it passes; the handle owns its device
+ *    hierarchy (or borrows the caller's arena, chhs_create_ext).
+ *  - Every call returns a chhs_status; on an error the handle stays usable and
+ *    chhs_last_error() describes it.  A handle is used by one host thread at a
+ *    time.
+ */
+#ifndef CHHS_H
+#define CHHS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chhs chhs_t; /* opaque handle: one run and its multigrid hierarchy */
+
+typedef enum {
+    CHHS_OK = 0,
+    CHHS_ERR_INVALID_ARG = 1,   /* bad dimension, size, parameter or pointer */
+    CHHS_ERR_OOM = 2,           /* device allocation failed, or the arena is too small */
+    CHHS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    CHHS_ERR_NOT_CONVERGED = 4, /* max_v V-cycles without reaching tol; state not advanced */
+    CHHS_ERR_DIVERGED = 5       /* non-finite or exploding residual; state not advanced */
+} chhs_status;
+
+/* Solver options.  The paper's FAS parameters (Section 5 preamble) are the
+ * defaults: V-cycles with nu1 = nu2 = 2 smoothing sweeps, tolerance 1e-10,
+ * coarsest grid 2 cells per direction. */
+typedef struct {
+    int nu1;       /* pre-smoothing sweeps per level (default 2) */
+    int nu2;       /* post-smoothing sweeps per level (default 2) */
+    int max_v;     /* V-cycles per step before CHHS_ERR_NOT_CONVERGED (default 50) */
+    int coarsest;  /* coarsening stops before a direction would drop below this (default 2) */
+    double tol;    /* stopping norm: sqrt(mean over cells of r_phi^2 + r_mu^2 + (s r_p)^2) (default 1e-10) */
+    int precision; /* 0: double-precision V-cycles; 1: single-precision V-cycles inside a
+                      double-precision defect-correction loop (same tol, measured in double) */
+} chhs_opts;
+
+/* Fill *opts with the defaults above.  Returns CHHS_ERR_INVALID_ARG on NULL. */
+chhs_status chhs_default_opts(chhs_opts* opts);
+
+/* Device bytes the handle's hierarchy needs (levels, coefficients, scratch):
+ * the admission figure for a memory budget.  0 for invalid arguments. */
+size_t chhs_workspace_bytes(int dim, const int n[3], const chhs_opts* opts);
+
+/* Create a run of dimension dim (2 or 3) on an n[0] x n[1] (x n[2]) grid of
+ * spacing h > 0 with interface width eps > 0, coupling gamma >= 0 and time
+ * step dt > 0 (Section 2).  Every n[a] must be >= 2.  opts NULL means the
+ * defaults.  cuda_stream (a cudaStream_t, NULL = a stream the handle creates)
+ * orders all of the handle's device work.  Allocates the hierarchy with
+ * cudaMalloc.  The state starts at phi^0 = phi^{-1} = 0 until chhs_set_phi. */
+chhs_status chhs_create(int dim, const int n[3], double h, double eps, double gamma, double dt,
+                        const chhs_opts* opts, void* cuda_stream, chhs_t** out);
+
+/* As chhs_create, but the hierarchy lives in the caller's device buffer
+ * `arena` of `arena_bytes` (>= chhs_workspace_bytes, 256-byte aligned), which
+ * must outlive the handle.  The handle allocates no device memory of its own
+ * apart from its CUDA graph. */
+chhs_status chhs_create_ext(int dim, const int n[3], double h, double eps, double gamma, double dt,
+                            const chhs_opts* opts, void* cuda_stream, void* arena, size_t arena_bytes,
+                            chhs_t** out);
+
+/* Set the two starting levels (Remark 2.2): phi^m = phi0 and
+ * phi^{m-1} = phi_prev, or phi^{m-1} = phi0 when phi_prev is NULL.  Resets
+ * mu and p (the warm starts of the next solve) to zero. */
+chhs_status chhs_set_phi(chhs_t* run, const double* phi0, const double* phi_prev, int on_device);
+
+/* Advance nsteps time steps (one FAS solve each).  vcycles_out (nullable):
+ * V-cycles summed over the steps taken; resid_out (nullable): the last
+ * stopping norm.  Stops at the first step that fails (NOT_CONVERGED or
+ * DIVERGED), leaving phi^m, phi^{m-1} at the last accepted step. */
+chhs_status chhs_step(chhs_t* run, int nsteps, int* vcycles_out, double* resid_out);
+
+/* The asynchronous half of chhs_step: enqueue nsteps steps on the handle's
+ * stream and return without waiting.  The caller may record events around
+ * it.  Call chhs_wait before any other call on the handle. */
+chhs_status chhs_step_async(chhs_t* run, int nsteps);
+
+/* Wait for the steps enqueued by chhs_step_async; outputs and status as
+ * chhs_step. */
+chhs_status chhs_wait(chhs_t* run, int* vcycles_out, double* resid_out);
+
+/* Kernel launches of one time step's graph: *per_vcycle for each V-cycle and
+ * *per_step for the frame around the V-cycle loop (setup, restrictions of
+ * phi^m and phi*, the initial norm, the mean of p and the accepted step).
+ * A step with V cycles launches per_step + V * per_vcycle kernels. */
+chhs_status chhs_launch_counts(const chhs_t* run, int* per_vcycle, int* per_step);
+
+/* Kernel kinds reported by chhs_profile_step. */
+enum {
+    CHHS_K_SMOOTH = 0,      /* one colour pass of the nonlinear Gauss-Seidel smoother; units: cells updated */
+    CHHS_K_RESTRICT = 1,    /* residual + restriction to the next level; units: fine cells */
+    CHHS_K_COARSE_RHS = 2,  /* FAS coarse right-hand side; units: coarse cells */
+    CHHS_K_PROLONG = 3,     /* prolongation + correction; units: fine cells */
+    CHHS_K_COARSEST = 4,    /* coarsest-grid solve; units: 1 per launch */
+    CHHS_K_NORM = 5,        /* stopping norm on the finest grid; units: cells */
+    CHHS_K_FRAME = 6,       /* setup, coefficient restriction, mean of p, accept; units: launches */
+    CHHS_K_COUNT = 7
+};
+
+/* Advance one time step exactly as chhs_step(run, 1) does, but launch the
+ * kernels one by one (no graph) with a CUDA event pair around each, and add
+ * into the caller's arrays of CHHS_K_COUNT entries: device milliseconds,
+ * launches and work units per kernel kind.  For profiling only: the host
+ * reads the stopping norm after every V-cycle. */
+chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_out, double* units_out);
+
+/* Discrete mass (phi^m, 1) = h^d sum phi^m (Section 4, mass conservation). */
+chhs_status chhs_mass(chhs_t* run, double* mass_out);
+
+/* E_h(phi^m) (Eq. 2.8) and, if F_out is not NULL, F_h(phi^m, phi^{m-1}) (Eq. 2.9). */
+chhs_status chhs_energy(chhs_t* run, double* E_out, double* F_out);
+
+/* Copy out phi^m (the latest accepted step). */
+chhs_status chhs_get_phi(chhs_t* run, double* out, int on_device);
+
+/* Copy out the full state: phi^m, phi^{m-1}, mu^{m-1/2}, p^{m-1/2} (each
+ * nullable; p has zero mean).  With chhs_set_state this is a checkpoint. */
+chhs_status chhs_get_state(chhs_t* run, double* phi, double* phi_prev, double* mu, double* p,
+                           int on_device);
+
+/* Restore a state written by chhs_get_state; mu and p may be NULL (then zero). */
+chhs_status chhs_set_state(chhs_t* run, const double* phi, const double* phi_prev, const double* mu,
+                           const double* p, int on_device);
+
+/* Number of multigrid levels of the handle (finest included). */
+int chhs_num_levels(const chhs_t* run);
+
+/* Release the handle and its device memory (not a caller's arena). NULL is a no-op. */
+void chhs_destroy(chhs_t* run);
+
+/* Text of the last error of this handle ("" if none); valid until the next call. */
+const char* chhs_last_error(const chhs_t* run);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHHS_H */

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of the C ABI in ``include/chhs.h`` (``libchhs.so``).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Functions keep the C names (``chhs_create``, ``chhs_step``, ``chhs_mass``,
+``chhs_energy`` ...); ``Run`` wraps a handle for convenience.  Arrays are
+numpy float64 (host) or CUDA torch float64 tensors (device), C-contiguous,
+indexed [y, x] or [z, y, x] (x fastest).
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1611_02967_gb300.build``); loading raises if it is missing.
+There is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchhs.so")
+
+CHHS_OK, CHHS_ERR_INVALID_ARG, CHHS_ERR_OOM, CHHS_ERR_CUDA, CHHS_ERR_NOT_CONVERGED, CHHS_ERR_DIVERGED = range(6)
+STATUS_NAMES = {0: "CHHS_OK", 1: "CHHS_ERR_INVALID_ARG", 2: "CHHS_ERR_OOM", 3: "CHHS_ERR_CUDA",
+                4: "CHHS_ERR_NOT_CONVERGED", 5: "CHHS_ERR_DIVERGED"}
+
+EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_create_ext", "chhs_set_phi",
+           "chhs_step", "chhs_step_async", "chhs_wait", "chhs_launch_counts", "chhs_profile_step",
+           "chhs_mass", "chhs_energy", "chhs_get_phi", "chhs_get_state", "chhs_set_state",
+           "chhs_num_levels", "chhs_destroy", "chhs_last_error"]
+
+# kernel kinds of chhs_profile_step
+K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "coarsest", "norm", "frame"]
+
+
+class chhs_opts(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_v", ctypes.c_int),
+                ("coarsest", ctypes.c_int), ("tol", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class ChhsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+_vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    """Load libchhs.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libchhs.so not built: run python -m paper_1611_02967_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        i, d, sz = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        optp = ctypes.POINTER(chhs_opts)
+        sig = {
+            "chhs_default_opts": (i, [optp]),
+            "chhs_workspace_bytes": (sz, [i, _ip, optp]),
+            "chhs_create": (i, [i, _ip, d, d, d, d, optp, _vp, ctypes.POINTER(_vp)]),
+            "chhs_create_ext": (i, [i, _ip, d, d, d, d, optp, _vp, _vp, sz, ctypes.POINTER(_vp)]),
+            "chhs_set_phi": (i, [_vp, _vp, _vp, i]),
+            "chhs_step": (i, [_vp, i, _ip, _dp]),
+            "chhs_step_async": (i, [_vp, i]),
+            "chhs_wait": (i, [_vp, _ip, _dp]),
+            "chhs_launch_counts": (i, [_vp, _ip, _ip]),
+            "chhs_profile_step": (i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
+            "chhs_mass": (i, [_vp, _dp]),
+            "chhs_energy": (i, [_vp, _dp, _dp]),
+            "chhs_get_phi": (i, [_vp, _vp, i]),
+            "chhs_get_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
+            "chhs_set_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
+            "chhs_num_levels": (i, [_vp]),
+            "chhs_destroy": (None, [_vp]),
+            "chhs_last_error": (ctypes.c_char_p, [_vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_opts(**kw):
+    o = chhs_opts()
+    lib().chhs_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _dims(shape):
+    n = list(shape[::-1]) + [1] * (3 - len(shape))
+    return len(shape), (ctypes.c_int * 3)(*n)
+
+
+def _buf(a, n, writable=False):
+    """(pointer, on_device, keepalive) for a numpy array or CUDA torch tensor of n doubles."""
+    if a is None:
+        return None, 0, None
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous() or a.numel() != n:
+            raise ValueError("need a contiguous float64 tensor of %d elements" % n)
+        return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0), a
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags.c_contiguous or arr.size != n:
+        if writable:
+            raise ValueError("need a C-contiguous float64 array of %d elements" % n)
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+        if arr.size != n:
+            raise ValueError("need %d elements" % n)
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+def workspace_bytes(shape, opts=None):
+    dim, n = _dims(shape)
+    return lib().chhs_workspace_bytes(dim, n, ctypes.byref(opts) if opts is not None else None)
+
+
+class Run:
+    """One CHHS run (a chhs_t handle)."""
+
+    def __init__(self, shape, h, eps, gamma, dt, opts=None, stream=None, arena=None):
+        self.shape = tuple(int(x) for x in shape)
+        self.ncell = int(np.prod(self.shape))
+        self.h, self.eps, self.gamma, self.dt = float(h), float(eps), float(gamma), float(dt)
+        dim, n = _dims(self.shape)
+        handle = ctypes.c_void_p()
+        optp = ctypes.byref(opts) if opts is not None else None
+        st = ctypes.c_void_p(stream) if stream else None
+        self._arena = arena
+        if arena is not None:
+            s = lib().chhs_create_ext(dim, n, self.h, self.eps, self.gamma, self.dt, optp, st,
+                                      ctypes.c_void_p(arena.data_ptr()), arena.numel() * arena.element_size(),
+                                      ctypes.byref(handle))
+        else:
+            s = lib().chhs_create(dim, n, self.h, self.eps, self.gamma, self.dt, optp, st, ctypes.byref(handle))
+        if s != CHHS_OK:
+            raise ChhsError(s, "chhs_create failed")
+        self.handle = handle
+
+    def _check(self, s):
+        if s != CHHS_OK:
+            raise ChhsError(s, lib().chhs_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().chhs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def num_levels(self):
+        return lib().chhs_num_levels(self.handle)
+
+    def set_phi(self, phi0, phi_prev=None):
+        p0, dev0, k0 = _buf(phi0, self.ncell)
+        p1, dev1, k1 = _buf(phi_prev, self.ncell)
+        if phi_prev is not None and dev0 != dev1:
+            raise ValueError("phi0 and phi_prev must both be host or both be device")
+        self._check(lib().chhs_set_phi(self.handle, p0, p1, dev0))
+
+    def step(self, nsteps=1, check=True):
+        """Advance nsteps; returns (status, total V-cycles, last residual)."""
+        v = ctypes.c_int(0)
+        r = ctypes.c_double(0.0)
+        s = lib().chhs_step(self.handle, int(nsteps), ctypes.byref(v), ctypes.byref(r))
+        if check:
+            self._check(s)
+        return s, v.value, r.value
+
+    def step_async(self, nsteps=1):
+        self._check(lib().chhs_step_async(self.handle, int(nsteps)))
+
+    def wait(self, check=True):
+        v = ctypes.c_int(0)
+        r = ctypes.c_double(0.0)
+        s = lib().chhs_wait(self.handle, ctypes.byref(v), ctypes.byref(r))
+        if check:
+            self._check(s)
+        return s, v.value, r.value
+
+    def launch_counts(self):
+        """(kernels per V-cycle, kernels per step outside the V-cycle loop)."""
+        a = ctypes.c_int(0)
+        b = ctypes.c_int(0)
+        self._check(lib().chhs_launch_counts(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def profile_step(self, acc=None):
+        """One step launched kernel by kernel with events; accumulates into
+        acc = {kind: [ms, launches, units]} and returns it."""
+        n = len(K_NAMES)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_longlong * n)()
+        un = (ctypes.c_double * n)()
+        self._check(lib().chhs_profile_step(self.handle, ms, la, un))
+        acc = acc if acc is not None else {k: [0.0, 0, 0.0] for k in K_NAMES}
+        for q, k in enumerate(K_NAMES):
+            acc[k][0] += ms[q]
+            acc[k][1] += la[q]
+            acc[k][2] += un[q]
+        return acc
+
+    def mass(self):
+        m = ctypes.c_double(0.0)
+        self._check(lib().chhs_mass(self.handle, ctypes.byref(m)))
+        return m.value
+
+    def energy(self):
+        E = ctypes.c_double(0.0)
+        F = ctypes.c_double(0.0)
+        self._check(lib().chhs_energy(self.handle, ctypes.byref(E), ctypes.byref(F)))
+        return E.value, F.value
+
+    def get_phi(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, dev, _ = _buf(out, self.ncell, writable=True)
+        self._check(lib().chhs_get_phi(self.handle, p, dev))
+        return out
+
+    def get_state(self):
+        """(phi^m, phi^{m-1}, mu, p) as host arrays."""
+        outs = [np.empty(self.shape) for _ in range(4)]
+        ptrs = [_buf(o, self.ncell, writable=True)[0] for o in outs]
+        self._check(lib().chhs_get_state(self.handle, *ptrs, 0))
+        return tuple(outs)
+
+    def set_state(self, phi, phi_prev, mu=None, p=None):
+        bufs = [_buf(a, self.ncell) for a in (phi, phi_prev, mu, p)]
+        devs = {b[1] for b in bufs if b[0] is not None}
+        if len(devs) > 1:
+            raise ValueError("mixed host and device buffers")
+        self._check(lib().chhs_set_state(self.handle, *[b[0] for b in bufs], devs.pop()))

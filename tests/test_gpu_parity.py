@@ -1,0 +1,152 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+The red-black GPU smoother and the lexicographic oracle walk different
+iterates to the same unique solution of (2.5)-(2.7) (Theorem 2.1), so every
+comparison is on converged steps from identical inputs: the GPU's own
+(phi^m, phi^{m-1}) are handed to the oracle, which solves that one step to
+1e-13, and the GPU's phi^{m+1} must agree within 1e-9 (double-precision path).
+mu is compared too; p is compared modulo its constant (pure Neumann).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1611_02967_gb300 import chhs, inputs
+
+pytestmark = pytest.mark.gpu
+
+PHI_TOL = 1e-9
+
+
+def _oracle_prm(h, eps, gamma, dt):
+    return oracle.Params(h, eps, gamma, dt, tol=1e-13, max_v=100)
+
+
+def _check_step(run, h, eps, gamma, dt, tol_phi=PHI_TOL):
+    """Take one GPU step from the run's current state and compare it with the oracle."""
+    phim, phimm1, mu_prev, p_prev = run.get_state()
+    run.step(1)
+    gphi, gphim, gmu, gp = run.get_state()
+    assert np.array_equal(gphim, phim)  # the accepted step rotated the levels
+    ophi, omu, op, v, r, st = oracle.step(phim, phimm1, _oracle_prm(h, eps, gamma, dt),
+                                          2.0 * phim - phimm1, mu_prev, p_prev)
+    assert st == oracle.OK
+    dphi = np.max(np.abs(gphi - ophi))
+    dmu = np.max(np.abs(gmu - omu))
+    dp = np.max(np.abs((gp - gp.mean()) - (op - op.mean())))
+    assert dphi <= tol_phi, (dphi, dmu, dp)
+    assert dmu <= 100 * tol_phi, (dphi, dmu, dp)
+    assert dp <= 1e4 * tol_phi, (dphi, dmu, dp)
+    return dphi
+
+
+@pytest.mark.parametrize("shape,h,eps,gamma,dt", [
+    ((16, 16), 0.2, 0.1, 2.0, 0.02),
+    ((24, 40), 0.1, 0.08, 1.0, 0.01),      # ragged: 960 cells, coarsens to 3 x 5
+    ((64, 32), 0.05, 0.05, 1.0, 0.01),     # non-square, several tiles
+    ((2, 2), 0.5, 0.2, 1.0, 0.01),         # single level: the coarsest solve only
+    ((8, 8, 8), 0.2, 0.1, 2.0, 0.01),
+    ((16, 8, 12), 0.1, 0.08, 4.0, 0.005),  # 3D, uneven
+])
+def test_single_steps_match_oracle(shape, h, eps, gamma, dt):
+    phi0 = inputs.spinodal(shape, 101, mean=0.0, amplitude=0.5)
+    with chhs.Run(shape, h, eps, gamma, dt) as run:
+        run.set_phi(phi0)
+        for _ in range(3):
+            _check_step(run, h, eps, gamma, dt)
+
+
+def test_spinodal64_every_step():
+    """The 64x64 spinodal workload (eps 0.05, gamma 1, dt 0.01, 50 steps): every step."""
+    w = inputs.workload("spinodal64")
+    with chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"]) as run:
+        run.set_phi(w["phi0"])
+        worst = 0.0
+        for k in range(w["steps"]):
+            worst = max(worst, _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"]))
+        print("spinodal64 worst max|dphi| over 50 steps: %.3e" % worst)
+
+
+def test_spinodal512_sampled_steps():
+    """The 512x512 workload at full size, steps sampled across the run (oracle one step each)."""
+    w = inputs.workload("spinodal512")
+    with chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"]) as run:
+        run.set_phi(w["phi0"])
+        done = 0
+        for target in (0, 40, 120):
+            if target > done:
+                run.step(target - done)
+                done = target
+            _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"])
+            done += 1
+
+
+def test_bubbles128_one_step():
+    """The 128^3 bubble workload at full size: the first step and a later one."""
+    w = inputs.workload("bubbles128")
+    with chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"]) as run:
+        run.set_phi(w["phi0"])
+        _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"])
+        run.step(5)
+        _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"])
+
+
+def test_mass_energy_match_oracle_and_invariants():
+    w = inputs.workload("spinodal64")
+    h, eps = w["h"], w["eps"]
+    with chhs.Run(w["shape"], h, eps, w["gamma"], w["dt"]) as run:
+        run.set_phi(w["phi0"])
+        m0 = run.mass()
+        assert abs(m0 - oracle.mass(w["phi0"], h)) < 1e-13
+        F_prev = None
+        for k in range(20):
+            run.step(1)
+            phim, phimm1, _, _ = run.get_state()
+            E, F = run.energy()
+            oE, oF = oracle.energy(phim, h, eps, phimm1)
+            assert abs(E - oE) < 1e-12 * max(1.0, abs(oE))
+            assert abs(F - oF) < 1e-12 * max(1.0, abs(oF))
+            # mass drift per step bounded by |Omega| * tol (+ roundoff)
+            area = phim.size * h * h
+            assert abs(run.mass() - m0) <= (k + 1) * area * 1.1e-10
+            if F_prev is not None:
+                assert F <= F_prev + 1e-12
+            F_prev = F
+
+
+def test_not_converged_keeps_state():
+    shape = (32, 32)
+    phi0 = inputs.spinodal(shape, 7, mean=0.0, amplitude=0.5)
+    opts = chhs.default_opts(max_v=1)
+    with chhs.Run(shape, 0.1, 0.05, 1.0, 0.01, opts=opts) as run:
+        run.set_phi(phi0)
+        s, v, r = run.step(3, check=False)
+        assert s == chhs.CHHS_ERR_NOT_CONVERGED
+        assert v == 1 and r > 1e-10
+        phim, phimm1, _, _ = run.get_state()
+        assert np.array_equal(phim, phi0) and np.array_equal(phimm1, phi0)
+
+
+def test_checkpoint_resume_bitwise():
+    shape, h, eps, gamma, dt = (32, 32), 0.1, 0.05, 2.0, 0.01
+    phi0 = inputs.spinodal(shape, 9, mean=0.0, amplitude=0.3)
+    with chhs.Run(shape, h, eps, gamma, dt) as a:
+        a.set_phi(phi0)
+        a.step(4)
+        state = a.get_state()
+        a.step(3)
+        ref = a.get_phi()
+    with chhs.Run(shape, h, eps, gamma, dt) as b:
+        b.set_state(*state)
+        b.step(3)
+        assert np.array_equal(b.get_phi(), ref)
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(chhs.ChhsError):
+        chhs.Run((16, 16), -0.1, 0.05, 1.0, 0.01)
+    with pytest.raises(chhs.ChhsError):
+        chhs.Run((1, 16), 0.1, 0.05, 1.0, 0.01)
+    with pytest.raises(chhs.ChhsError):
+        chhs.Run((16, 16), 0.1, 0.05, -1.0, 0.01)
+    assert chhs.workspace_bytes((512, 512)) > 11 * 512 * 512 * 8
