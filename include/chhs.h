@@ -147,6 +147,35 @@ chhs_status chhs_get_state(chhs_t* run, double* phi, double* phi_prev, double* m
 chhs_status chhs_set_state(chhs_t* run, const double* phi, const double* phi_prev, const double* mu,
                            const double* p, int on_device);
 
+/* Largest grid (in cells) chhs_energy_noalloc accepts. */
+#define CHHS_NOALLOC_MAX_CELLS (1 << 22)
+
+/* Mass and energies of device-resident fields without allocating memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc, such as a host framework whose memory pool owns the device, or
+ * a latency-bound loop that cannot take the device-wide synchronisation an
+ * allocation may cause.  It needs no handle.
+ *
+ * phi_dev, psi_dev: device pointers to dim-dimensional grids of n[0] x n[1]
+ * (x n[2]) doubles, x fastest (psi_dev NULL means psi = phi).  Outputs
+ * (nullable host pointers): mass_out = (phi, 1), E_out = E_h(phi) (Eq. 2.8),
+ * F_out = F_h(phi, psi) (Eq. 2.9), the same quantities chhs_mass and
+ * chhs_energy report for a handle's phi^m and phi^{m-1}.  Work is ordered
+ * on cuda_stream (NULL = the legacy default stream); the call waits for it.
+ *
+ * Scratch: a fixed device array of about 0.8 MB inside the library, held by
+ * every GPU that loads it until the process exits; grids above
+ * CHHS_NOALLOC_MAX_CELLS cells return CHHS_ERR_INVALID_ARG, as do a
+ * dimension other than 2 or 3, a size below 1, h <= 0 or eps <= 0.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call outside any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (on different
+ * streams, or from several host threads) race and must be serialised by the
+ * caller.  Returns CHHS_ERR_CUDA if a CUDA call fails. */
+chhs_status chhs_energy_noalloc(int dim, const int n[3], double h, double eps, const double* phi_dev,
+                                const double* psi_dev, void* cuda_stream, double* mass_out,
+                                double* E_out, double* F_out);
+
 /* Number of multigrid levels of the handle (finest included). */
 int chhs_num_levels(const chhs_t* run);
 

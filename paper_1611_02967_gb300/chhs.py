@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "CHHS_OK", 1: "CHHS_ERR_INVALID_ARG", 2: "CHHS_ERR_OOM", 3: "
 EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_create_ext", "chhs_set_phi",
            "chhs_step", "chhs_step_async", "chhs_wait", "chhs_launch_counts", "chhs_profile_step",
            "chhs_mass", "chhs_energy", "chhs_get_phi", "chhs_get_state", "chhs_set_state",
-           "chhs_num_levels", "chhs_destroy", "chhs_last_error"]
+           "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "coarsest", "norm", "frame"]
@@ -74,6 +74,7 @@ def lib():
             "chhs_num_levels": (i, [_vp]),
             "chhs_destroy": (None, [_vp]),
             "chhs_last_error": (ctypes.c_char_p, [_vp]),
+            "chhs_energy_noalloc": (i, [i, _ip, d, d, _vp, _vp, _vp, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -113,6 +114,23 @@ def _buf(a, n, writable=False):
         if arr.size != n:
             raise ValueError("need %d elements" % n)
     return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+def energy_noalloc(phi, psi, h, eps, stream=None):
+    """(mass, E_h(phi), F_h(phi, psi)) of CUDA float64 tensors, computed with
+    the library's fixed scratch array and no device allocation."""
+    n = int(np.prod(phi.shape))
+    p0, dev0, _ = _buf(phi, n)
+    p1, dev1, _ = _buf(psi, n)
+    if not dev0 or (psi is not None and not dev1):
+        raise ValueError("phi and psi must be CUDA tensors")
+    dim, nn = _dims(tuple(phi.shape))
+    m, E, F = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    s = lib().chhs_energy_noalloc(dim, nn, float(h), float(eps), p0, p1, ctypes.c_void_p(stream) if stream else None,
+                                  ctypes.byref(m), ctypes.byref(E), ctypes.byref(F))
+    if s != CHHS_OK:
+        raise ChhsError(s, "chhs_energy_noalloc failed")
+    return m.value, E.value, F.value
 
 
 def workspace_bytes(shape, opts=None):

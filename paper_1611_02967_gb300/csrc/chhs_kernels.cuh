@@ -297,7 +297,7 @@ __device__ __forceinline__ void sum_partials(const double* partials, int nparts,
 
 // Finish the stopping norm.  mode 0: start of a step (records r0); mode 1:
 // after a V-cycle (counts it).  Sets the while-loop condition of the step graph.
-__global__ void k_resid_finish(const double* partials, int nparts, int ncell, DevState* st,
+static __global__ void k_resid_finish(const double* partials, int nparts, int ncell, DevState* st,
                                cudaGraphConditionalHandle cond, int mode, int use_cond) {
   double tot[1];
   sum_partials<1>(partials, nparts, tot);
@@ -358,21 +358,21 @@ __global__ void __launch_bounds__(kBlock) k_setup(Level<double> L, const double*
 }
 
 // Partial sums of v (NV = 1), one per block.
-__global__ void __launch_bounds__(kBlock) k_sum_partial(const double* v, int n, double* partials) {
+static __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* v, int n, double* partials) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {c < n ? v[c] : 0.0};
   block_sum<1>(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
 }
 
-__global__ void k_mean_finish(const double* partials, int nparts, int n, DevState* st) {
+static __global__ void k_mean_finish(const double* partials, int nparts, int n, DevState* st) {
   double tot[1];
   sum_partials<1>(partials, nparts, tot);
   if (threadIdx.x == 0) st->pmean = tot[0] / n;
 }
 
 // Accept the step: phi^{m-1} <- phi^m, phi^m <- phi^{m+1}, p <- p - mean(p).
-__global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, double* phimm1, DevState* st) {
+static __global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, double* phimm1, DevState* st) {
   if (st->failed) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c == 0) {
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kBlock) k_energy_partial(const double* phi, co
     for (int q = 0; q < 6; ++q) partials[blockIdx.x * 6 + q] = v[q];
 }
 
-__global__ void k_energy_finish(const double* partials, int nparts, DevState* st) {
+static __global__ void k_energy_finish(const double* partials, int nparts, DevState* st) {
   double tot[6];
   sum_partials<6>(partials, nparts, tot);
   if (threadIdx.x == 0)
