@@ -53,12 +53,19 @@ std::vector<Shape> level_shapes(int dim, const int n[3], int coarsest) {
   return out;
 }
 
-constexpr int kLevelFields = 11;  // phi mu p fphi fmu fp phim phis phi0 mu0 p0
+// phi mu p fphi fmu fp phim phis phi0 mu0 p0, ax ay Mx My, sM sa, cAe cCD cG (+ az Mz in 3D)
+constexpr int kBaseFields = 11;
+int level_fields(int dim) { return kBaseFields + (dim == 3 ? 11 : 9); }
+
+// Levels with at most this many cells run inside the one-block tail kernel.
+// In double precision one SM does 2 FMA per clock, so only the tiniest levels
+// (8 x 8, 4 x 4 x 4) are cheaper there than as grid-wide launches.
+constexpr int kTailCellsF64 = 64;
 
 struct Layout {
   std::vector<Shape> shapes;
   size_t state_off, partial_off, phimm1_off;
-  std::vector<size_t> level_off;  // start of each level's kLevelFields arrays
+  std::vector<size_t> level_off;  // start of each level's field arrays
   size_t total;
   int nparts;  // partial-sum slots (blocks of the finest grid)
 };
@@ -78,7 +85,7 @@ Layout make_layout(int dim, const int n[3], int coarsest) {
   for (const Shape& s : L.shapes) {
     size_t nc = (size_t)s.n[0] * s.n[1] * s.n[2];
     L.level_off.push_back(off);
-    off += kLevelFields * align_up(sizeof(double) * nc);
+    off += level_fields(dim) * align_up(sizeof(double) * nc);
   }
   L.total = off;
   return L;
@@ -134,6 +141,8 @@ struct chhs {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<Level<double>> lev;
+  int tail_start = 0;   // first level run by the one-block tail kernel
+  Tail<double> tail{};  // its levels
   double* phimm1 = nullptr;
   DevState* st = nullptr;
   double* partials = nullptr;
@@ -191,47 +200,56 @@ struct Enqueue {
     return Coefs<double>{run->dt, run->gamma, 0.75 * run->eps * run->eps};
   }
 
-  static void smooth(chhs_t* run, cudaStream_t s, const Level<double>& L, int sweeps) {
+  // sweeps red-black sweeps; with rhs the first one also completes the FAS
+  // right-hand side of this (coarse) level.
+  static void smooth(chhs_t* run, cudaStream_t s, const Level<double>& L, int sweeps, bool rhs) {
     const Coefs<double> K = coefs(run);
+    const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
+    const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
     for (int it = 0; it < sweeps; ++it)
-      for (int colour = 0; colour < 2; ++colour)
+      for (int colour = 0; colour < 2; ++colour) {
+        const int with_rhs = (rhs && it == 0) ? 1 : 0;
         launch(run, s, CHHS_K_SMOOTH, colour_cells(L, colour), [&] {
-          k_smooth<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K, colour);
+          k_smooth<double, DIM, false><<<blocks, kSmoothBlock, 0, s>>>(L, K, colour, with_rhs);
         });
+      }
   }
 
   static void vcycle(chhs_t* run, cudaStream_t s, int l) {
     const Coefs<double> K = coefs(run);
-    const int nl = (int)run->lev.size();
     const Level<double>& L = run->lev[l];
-    if (l == nl - 1) {
-      launch(run, s, CHHS_K_COARSEST, 1.0, [&] { k_coarsest<double, DIM><<<1, kBlock, 0, s>>>(L, K); });
+    if (l == run->tail_start) {
+      launch(run, s, CHHS_K_COARSEST, 1.0, [&] {
+        k_tail<double, DIM, false><<<1, kTailThreads, 0, s>>>(run->tail, K);
+      });
       return;
     }
     const Level<double>& C = run->lev[l + 1];
-    smooth(run, s, L, run->opts.nu1);
+    const bool rhs = l > 0;
+    if (rhs && run->opts.nu1 == 0)
+      launch(run, s, CHHS_K_COARSE_RHS, L.ncell, [&] {
+        k_coarse_rhs<double, DIM, false><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K);
+      });
+    smooth(run, s, L, run->opts.nu1, rhs && run->opts.nu1 > 0);
+    constexpr int TX = DIM == 3 ? 8 : 16;
+    const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
+    const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
     launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
-      k_residual_restrict<double, DIM><<<nblocks(C.ncell), kBlock, 0, s>>>(L, C, K);
-    });
-    launch(run, s, CHHS_K_COARSE_RHS, C.ncell, [&] {
-      k_coarse_rhs<double, DIM><<<nblocks(C.ncell), kBlock, 0, s>>>(C, K);
+      k_residual_restrict<double, DIM, false><<<rblocks, kBlock, 0, s>>>(L, C, K);
     });
     vcycle(run, s, l + 1);
     launch(run, s, CHHS_K_PROLONG, L.ncell, [&] {
       k_prolong<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, C);
     });
-    smooth(run, s, L, run->opts.nu2);
+    smooth(run, s, L, run->opts.nu2, false);
   }
 
   static void norm(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int mode, int use_cond) {
     const Coefs<double> K = coefs(run);
     const Level<double>& L = run->lev[0];
     launch(run, s, CHHS_K_NORM, L.ncell, [&] {
-      k_resid_partial<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K, run->partials);
-    });
-    launch(run, s, CHHS_K_NORM, 0.0, [&] {
-      k_resid_finish<<<1, 1024, 0, s>>>(run->partials, nblocks(L.ncell), L.ncell, run->st, cond, mode,
-                                        use_cond);
+      k_norm<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K, run->partials, run->st, cond, mode,
+                                                              use_cond);
     });
   }
 
@@ -244,6 +262,11 @@ struct Enqueue {
       launch(run, s, CHHS_K_FRAME, 1.0, [&] {
         k_restrict_coef<double, DIM><<<nblocks(run->lev[l].ncell), kBlock, 0, s>>>(run->lev[l - 1],
                                                                                   run->lev[l]);
+      });
+    const Coefs<double> K = coefs(run);
+    for (size_t l = 0; l < run->lev.size(); ++l)
+      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+        k_coef<double, DIM><<<nblocks(run->lev[l].ncell), kBlock, 0, s>>>(run->lev[l], K);
       });
   }
 
@@ -352,19 +375,39 @@ chhs_status setup_handle(chhs_t* run) {
     size_t nc = (size_t)s.n[0] * s.n[1] * s.n[2];
     size_t stride = align_up(sizeof(double) * nc);
     char* base = run->arena + Lo.level_off[l];
-    double* f[kLevelFields];
-    for (int q = 0; q < kLevelFields; ++q) f[q] = reinterpret_cast<double*>(base + q * stride);
+    const int nf = level_fields(run->dim);
+    double* f[kBaseFields + 11];
+    for (int q = 0; q < nf; ++q) f[q] = reinterpret_cast<double*>(base + q * stride);
     Level<double> L;
     L.phi = f[0]; L.mu = f[1]; L.p = f[2];
     L.fphi = f[3]; L.fmu = f[4]; L.fp = f[5];
     L.phim = f[6]; L.phis = f[7];
     L.phi0 = f[8]; L.mu0 = f[9]; L.p0 = f[10];
+    L.ax = f[11]; L.ay = f[12]; L.Mx = f[13]; L.My = f[14];
+    L.sM = f[15]; L.sa = f[16];
+    L.cAe = f[17]; L.cCD = f[18]; L.cG = f[19];
+    L.az = run->dim == 3 ? f[20] : nullptr;
+    L.Mz = run->dim == 3 ? f[21] : nullptr;
+    L.phib = nullptr;
     L.nx = s.n[0]; L.ny = s.n[1]; L.nz = s.n[2];
     L.ncell = (int)nc;
     L.ih2 = 1.0 / (hl * hl);
+    L.h2 = hl * hl;
+    L.sih2 = run->dt * L.ih2;
+    L.e34ih2 = 0.75 * run->eps * run->eps * L.ih2;
     run->lev.push_back(L);
     hl *= 2.0;
   }
+  const int nl = (int)run->lev.size();
+  run->tail_start = nl - 1;
+  while (run->tail_start > 0 && run->lev[run->tail_start - 1].ncell <= kTailCellsF64 &&
+         nl - (run->tail_start - 1) <= kTailMaxLevels)
+    --run->tail_start;
+  run->tail.n = nl - run->tail_start;
+  for (int l = run->tail_start; l < nl; ++l) run->tail.lev[l - run->tail_start] = run->lev[l];
+  run->tail.nu1 = run->opts.nu1;
+  run->tail.nu2 = run->opts.nu2;
+  run->tail.top_rhs = run->tail_start > 0 ? 1 : 0;
   CU(cudaMemsetAsync(run->arena, 0, Lo.total, run->stream));
   CU(cudaMallocHost(&run->host_st, sizeof(DevState)));
   memset(run->host_st, 0, sizeof(DevState));

@@ -8,6 +8,14 @@
 // On the finest grid f = (phi^m, -phi* - (1/4) eps^2 Lap_h phi^{m-1}, 0); on a
 // coarse grid f is the FAS right-hand side R(f - N(u)) + N_c(R u).
 //
+// Correction form (CORR = true, used by the single-precision inner solves of
+// the mixed-precision path): the unknown is a correction e to a base state
+// with phi-part phi_b, and chi(phi, phi^m) becomes
+//   chi(phi_b + e, phi^m) - chi(phi_b, phi^m)
+//     = e (3 phi_b^2 + 2 phi_b phi^m + (phi^m)^2 + (3 phi_b + phi^m) e + e^2) / 4,
+// so that N(base + e) - N(base) is evaluated without cancellation; every other
+// term of N is linear and keeps its form.
+//
 // Grid functions are stored x fastest, interior cells only.  The homogeneous
 // Neumann ghosts of Appendix A (ghost = mirror of its neighbour) make every
 // boundary-face difference vanish, so boundary faces carry no flux and the
@@ -18,17 +26,29 @@
 
 namespace chhs_dev {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 256;        // block size of the plain per-cell kernels
+constexpr int kSmoothBlock = 128;  // block size of the smoother (more, smaller blocks per SM)
+constexpr int kTailThreads = 512;  // one block runs the coarse tail of a V-cycle
+constexpr int kTailMaxLevels = 12;
 
 template <typename T>
 struct Level {
-  T *phi, *mu, *p;     // unknowns
+  T *phi, *mu, *p;     // unknowns (the correction e in correction form)
   T *fphi, *fmu, *fp;  // right-hand sides
   T *phim, *phis;      // phi^m and phi* restricted to this level (fixed in a step)
+  T *phib;             // correction form only: phi-part of the base state
   T *phi0, *mu0, *p0;  // restricted iterate R u kept for the FAS correction
-  int nx, ny, nz;      // nz == 1 in 2D
+  // Coefficients fixed for a time step (k_coef): a = A_h phi* and M(a) on the
+  // +x, +y (+z) face of every cell (zero on boundary faces), their sums over a
+  // cell's interior faces, and the smoother's per-cell Ae, C/Dn and G.
+  T *ax, *ay, *az, *Mx, *My, *Mz;
+  T *sM, *sa;
+  T *cAe, *cCD, *cG;
+  int nx, ny, nz;  // nz == 1 in 2D
   int ncell;
-  T ih2;               // 1 / h^2 on this level
+  T ih2, h2;       // 1/h^2 and h^2 on this level
+  T sih2;          // s / h^2
+  T e34ih2;        // (3/4) eps^2 / h^2
 };
 
 template <typename T>
@@ -51,6 +71,8 @@ struct DevState {
   double r0;       // stopping norm at the start of the step
   double pmean;    // mean of p, removed when the step is accepted
   double diag[8];  // reduction results (mass, energies)
+  unsigned int ticket;  // blocks of the norm kernel that have finished
+  unsigned int pad_;
 };
 
 // chi(a, b) = (a^2 + b^2)(a + b) / 4 (Eq. 2.4) and d chi / d a.
@@ -59,6 +81,47 @@ __device__ __forceinline__ T chi(T a, T b) { return T(0.25) * (a * a + b * b) * 
 template <typename T>
 __device__ __forceinline__ T dchi_da(T a, T b) { return T(0.25) * (T(3) * a * a + T(2) * a * b + b * b); }
 
+// The nonlinear term of N2 at cell c for the unknown value v, and its
+// derivative in v (plain form, or correction form around phi_b).
+template <typename T, bool CORR>
+__device__ __forceinline__ T chi_term(const Level<T>& L, int c, T v, T pm) {
+  if (CORR) {
+    T b = L.phib[c];
+    return T(0.25) * v * (T(3) * b * b + T(2) * b * pm + pm * pm + (T(3) * b + pm) * v + v * v);
+  }
+  return chi(v, pm);
+}
+template <typename T, bool CORR>
+__device__ __forceinline__ T dchi_term(const Level<T>& L, int c, T v, T pm) {
+  return CORR ? dchi_da(L.phib[c] + v, pm) : dchi_da(v, pm);
+}
+
+// Approximate reciprocal of x >= 1 (the PTX rcp.approx instruction).  It
+// scales the smoother's local Newton update only: an inexact local Jacobian
+// changes how fast the sweep contracts, never its fixed point (zero residual).
+__device__ __forceinline__ double rcp_approx(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// n and 1/n for the interior-face count n in 1..6, by selection (no
+// conversion or division instructions).
+template <typename T>
+__device__ __forceinline__ T count_value(int n) {
+  return n == 4 ? T(4) : n == 2 ? T(2) : n == 3 ? T(3) : n == 6 ? T(6) : n == 5 ? T(5) : T(1);
+}
+template <typename T>
+__device__ __forceinline__ T inv_count(int n) {
+  return n == 4 ? T(0.25) : n == 2 ? T(0.5) : n == 3 ? T(1.0 / 3.0) : n == 6 ? T(1.0 / 6.0)
+         : n == 5 ? T(0.2) : T(1);
+}
+
 __device__ __forceinline__ void cell_ijk(int c, int nx, int ny, int& i, int& j, int& k) {
   i = c % nx;
   int r = c / nx;
@@ -66,54 +129,97 @@ __device__ __forceinline__ void cell_ijk(int c, int nx, int ny, int& i, int& j, 
   k = r / ny;
 }
 
-// Face sums of one cell: for each interior face f with neighbour e,
-//   a_f = A_h phi* = (phi*_c + phi*_e)/2,  M_f = 1 + gamma a_f^2.
+// Neighbour sums of one cell over its interior faces f (neighbour e):
+//   Mmu = sum M_f mu_e, ap = sum a_f p_e, amu = sum a_f mu_e,
+//   phi = sum phi_e, p = sum p_e, m = n_c.
+// With sM = sum M_f and sa = sum a_f (k_coef), the face sums of N become
+//   sum M_f (mu_e - mu_c) = Mmu - sM mu_c,  sum a_f (p_e - p_c) = ap - sa p_c, ...
 template <typename T>
-struct Sums {
-  T Mdmu, adp, admu, dphi, dp, M, a;
-  int m;  // number of interior faces n_c
+struct Nb {
+  T Mmu, ap, amu, phi, p;
+  int m;
 };
 
 template <typename T, int DIM>
-__device__ __forceinline__ void face_sums(const Level<T>& L, const Coefs<T>& K, int c, int i, int j,
-                                          int k, T phic, T muc, T pc, T psc, Sums<T>& S) {
-  S.Mdmu = S.adp = S.admu = S.dphi = S.dp = S.M = S.a = T(0);
+__device__ __forceinline__ void nb_sums(const Level<T>& L, const T* phi, const T* mu, const T* p, int c,
+                                        int i, int j, int k, Nb<T>& S) {
+  S.Mmu = S.ap = S.amu = S.phi = S.p = T(0);
   S.m = 0;
-  auto face = [&](int e) {
-    T af = T(0.5) * (psc + L.phis[e]);
-    T Mf = T(1) + K.gamma * af * af;
-    T dmu = L.mu[e] - muc;
-    T dp = L.p[e] - pc;
-    S.Mdmu += Mf * dmu;
-    S.adp += af * dp;
-    S.admu += af * dmu;
-    S.dphi += L.phi[e] - phic;
-    S.dp += dp;
-    S.M += Mf;
-    S.a += af;
+  auto face = [&](int e, T a, T M) {
+    T mue = mu[e], pe = p[e];
+    S.Mmu += M * mue;
+    S.ap += a * pe;
+    S.amu += a * mue;
+    S.phi += phi[e];
+    S.p += pe;
     S.m += 1;
   };
   const int sy = L.nx, sz = L.nx * L.ny;
-  if (i > 0) face(c - 1);
-  if (i + 1 < L.nx) face(c + 1);
-  if (j > 0) face(c - sy);
-  if (j + 1 < L.ny) face(c + sy);
+  if (i > 0) face(c - 1, L.ax[c - 1], L.Mx[c - 1]);
+  if (i + 1 < L.nx) face(c + 1, L.ax[c], L.Mx[c]);
+  if (j > 0) face(c - sy, L.ay[c - sy], L.My[c - sy]);
+  if (j + 1 < L.ny) face(c + sy, L.ay[c], L.My[c]);
   if (DIM == 3) {
-    if (k > 0) face(c - sz);
-    if (k + 1 < L.nz) face(c + sz);
+    if (k > 0) face(c - sz, L.az[c - sz], L.Mz[c - sz]);
+    if (k + 1 < L.nz) face(c + sz, L.az[c], L.Mz[c]);
   }
 }
 
-// N(u) at cell c.
+// N(u) at cell c for the fields (phi, mu, p) given explicitly.
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void eval_N(const Level<T>& L, const Coefs<T>& K, const T* phi, const T* mu,
+                                       const T* p, int c, int i, int j, int k, T& n1, T& n2, T& n3) {
+  Nb<T> S;
+  nb_sums<T, DIM>(L, phi, mu, p, c, i, j, k, S);
+  T phic = phi[c], muc = mu[c], pc = p[c];
+  T sM = L.sM[c], sa = L.sa[c], mm = count_value<T>(S.m);
+  n1 = phic - L.sih2 * ((S.Mmu - sM * muc) + (S.ap - sa * pc));
+  n2 = muc - chi_term<T, CORR>(L, c, phic, L.phim[c]) + L.e34ih2 * (S.phi - mm * phic);
+  n3 = -L.ih2 * ((S.p - mm * pc) + K.gamma * (S.amu - sa * muc));
+}
+
+// Coefficients of a time step on one level, from phi*: the face values
+// a_f = (phi*_c + phi*_e)/2 and M_f = 1 + gamma a_f^2 on the +x/+y/+z faces,
+// sM = sum M_f and sa = sum a_f over the interior faces, and the smoother's
+//   Ae = (s/h^2)(sM - gamma sa^2 / n_c),  C/Dn = s sa / n_c,  G = gamma sa / h^2.
 template <typename T, int DIM>
-__device__ __forceinline__ void apply_N(const Level<T>& L, const Coefs<T>& K, int c, int i, int j,
-                                        int k, T& n1, T& n2, T& n3) {
-  T phic = L.phi[c], muc = L.mu[c], pc = L.p[c];
-  Sums<T> S;
-  face_sums<T, DIM>(L, K, c, i, j, k, phic, muc, pc, L.phis[c], S);
-  n1 = phic - K.s * L.ih2 * (S.Mdmu + S.adp);
-  n2 = muc - chi(phic, L.phim[c]) + K.e34 * L.ih2 * S.dphi;
-  n3 = -L.ih2 * (S.dp + K.gamma * S.admu);
+__global__ void __launch_bounds__(kBlock) k_coef(Level<T> L, Coefs<T> K) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.ncell) return;
+  int i, j, k;
+  cell_ijk(c, L.nx, L.ny, i, j, k);
+  const T ps = L.phis[c];
+  T sumM = 0, suma = 0;
+  int m = 0;
+  auto face = [&](int e, T* a_out, T* M_out) {
+    T a = T(0.5) * (ps + L.phis[e]);
+    T M = T(1) + K.gamma * a * a;
+    sumM += M;
+    suma += a;
+    m += 1;
+    if (a_out) {
+      a_out[c] = a;
+      M_out[c] = M;
+    }
+  };
+  const int sy = L.nx, sz = L.nx * L.ny;
+  if (i > 0) face(c - 1, nullptr, nullptr);
+  if (i + 1 < L.nx) face(c + 1, L.ax, L.Mx);
+  else L.ax[c] = L.Mx[c] = T(0);
+  if (j > 0) face(c - sy, nullptr, nullptr);
+  if (j + 1 < L.ny) face(c + sy, L.ay, L.My);
+  else L.ay[c] = L.My[c] = T(0);
+  if (DIM == 3) {
+    if (k > 0) face(c - sz, nullptr, nullptr);
+    if (k + 1 < L.nz) face(c + sz, L.az, L.Mz);
+    else L.az[c] = L.Mz[c] = T(0);
+  }
+  T im = inv_count<T>(m);
+  L.sM[c] = sumM;
+  L.sa[c] = suma;
+  L.cAe[c] = L.sih2 * (sumM - K.gamma * suma * suma * im);
+  L.cCD[c] = K.s * suma * im;
+  L.cG[c] = K.gamma * L.ih2 * suma;
 }
 
 // ---------------------------------------------------------------- smoother
@@ -127,82 +233,135 @@ __device__ __forceinline__ void apply_N(const Level<T>& L, const Coefs<T>& K, in
 //   Dn = n_c / h^2,        B = chi_a(phi, phi^m) + (3/4) eps^2 n_c / h^2,
 //   Ae = A - C G / Dn = (s/h^2)(sum M_f - gamma (sum a_f)^2 / n_c) >= s n_c / h^2,
 //   dphi = (R1 - Ae R2 - (C/Dn) R3) / (1 + Ae B),  dmu = R2 + B dphi,
-//   dp = (R3 - G dmu) / Dn.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_smooth(Level<T> L, Coefs<T> K, int colour) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.ncell) return;
-  int i, j, k;
-  cell_ijk(c, L.nx, L.ny, i, j, k);
-  if (((i + j + k) & 1) != colour) return;
-  T phic = L.phi[c], muc = L.mu[c], pc = L.p[c], phimc = L.phim[c];
-  Sums<T> S;
-  face_sums<T, DIM>(L, K, c, i, j, k, phic, muc, pc, L.phis[c], S);
-  T n1 = phic - K.s * L.ih2 * (S.Mdmu + S.adp);
-  T n2 = muc - chi(phic, phimc) + K.e34 * L.ih2 * S.dphi;
-  T n3 = -L.ih2 * (S.dp + K.gamma * S.admu);
-  T R1 = L.fphi[c] - n1, R2 = L.fmu[c] - n2, R3 = L.fp[c] - n3;
-  T inv_m = T(1) / T(S.m);
-  T Ae = K.s * L.ih2 * (S.M - K.gamma * S.a * S.a * inv_m);
-  T CD = K.s * S.a * inv_m;
-  T G = K.gamma * L.ih2 * S.a;
-  T B = dchi_da(phic, phimc) + K.e34 * L.ih2 * T(S.m);
-  T dphi = (R1 - Ae * R2 - CD * R3) / (T(1) + Ae * B);
+//   dp = (R3 - G dmu) / Dn,
+// with R = f - N(u) at the cell.
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void cell_update(const Level<T>& L, const Coefs<T>& K, int c, int i, int j,
+                                            int k, T f1, T f2, T f3) {
+  Nb<T> S;
+  nb_sums<T, DIM>(L, L.phi, L.mu, L.p, c, i, j, k, S);
+  T phic = L.phi[c], muc = L.mu[c], pc = L.p[c], pm = L.phim[c];
+  T sM = L.sM[c], sa = L.sa[c], mm = count_value<T>(S.m);
+  T R1 = f1 - phic + L.sih2 * ((S.Mmu - sM * muc) + (S.ap - sa * pc));
+  T R2 = f2 - muc + chi_term<T, CORR>(L, c, phic, pm) - L.e34ih2 * (S.phi - mm * phic);
+  T R3 = f3 + L.ih2 * ((S.p - mm * pc) + K.gamma * (S.amu - sa * muc));
+  T Ae = L.cAe[c], CD = L.cCD[c], G = L.cG[c];
+  T B = dchi_term<T, CORR>(L, c, phic, pm) + L.e34ih2 * mm;
+  T dphi = (R1 - Ae * R2 - CD * R3) * rcp_approx(T(1) + Ae * B);
   T dmu = R2 + B * dphi;
-  T dp = (R3 - G * dmu) * inv_m / L.ih2;
+  T dp = (R3 - G * dmu) * (L.h2 * inv_count<T>(S.m));
   L.phi[c] = phic + dphi;
   L.mu[c] = muc + dmu;
   L.p[c] = pc + dp;
 }
 
-// ---------------------------------------------------------------- transfers
-
-// For each coarse cell: u_c = R u (mean of the 2^d children), kept twice (as
-// the coarse iterate and as u_c^0), and the restricted fine residual R r as
-// the first part of the FAS right-hand side.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_residual_restrict(Level<T> F, Level<T> C, Coefs<T> K) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= C.ncell) return;
-  int I, J, KK;
-  cell_ijk(q, C.nx, C.ny, I, J, KK);
-  T sphi = 0, smu = 0, sp = 0, r1 = 0, r2 = 0, r3 = 0;
-  const int kz = DIM == 3 ? 2 : 1;
-  for (int dk = 0; dk < kz; ++dk)
-    for (int dj = 0; dj < 2; ++dj)
-      for (int di = 0; di < 2; ++di) {
-        int i = 2 * I + di, j = 2 * J + dj, k = 2 * KK + dk;
-        int c = i + F.nx * (j + F.ny * k);
-        T n1, n2, n3;
-        apply_N<T, DIM>(F, K, c, i, j, k, n1, n2, n3);
-        r1 += F.fphi[c] - n1;
-        r2 += F.fmu[c] - n2;
-        r3 += F.fp[c] - n3;
-        sphi += F.phi[c];
-        smu += F.mu[c];
-        sp += F.p[c];
-      }
-  const T w = DIM == 3 ? T(0.125) : T(0.25);
-  C.phi[q] = C.phi0[q] = w * sphi;
-  C.mu[q] = C.mu0[q] = w * smu;
-  C.p[q] = C.p0[q] = w * sp;
-  C.fphi[q] = w * r1;
-  C.fmu[q] = w * r2;
-  C.fp[q] = w * r3;
+// The right-hand side at cell c for a smoothing pass.  With rhs set (the
+// first pre-smoothing sweep on a coarse level) it first completes the FAS
+// right-hand side f_c = R r + N_c(R u) from the saved R u (phi0, mu0, p0).
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void cell_rhs(const Level<T>& L, const Coefs<T>& K, int c, int i, int j, int k,
+                                         bool rhs, T& f1, T& f2, T& f3) {
+  f1 = L.fphi[c];
+  f2 = L.fmu[c];
+  f3 = L.fp[c];
+  if (rhs) {
+    T n1, n2, n3;
+    eval_N<T, DIM, CORR>(L, K, L.phi0, L.mu0, L.p0, c, i, j, k, n1, n2, n3);
+    f1 += n1;
+    f2 += n2;
+    f3 += n3;
+    L.fphi[c] = f1;
+    L.fmu[c] = f2;
+    L.fp[c] = f3;
+  }
 }
 
-// f_c += N_c(u_c^0): completes the FAS right-hand side on the coarse grid.
-template <typename T, int DIM>
+// Threads cover only the cells of the colour: ceil(nx/2) per grid row, the
+// row's first cell of the colour at i = (j + k + colour) & 1.
+template <typename T, int DIM, bool CORR>
+__global__ void __launch_bounds__(kSmoothBlock) k_smooth(Level<T> L, Coefs<T> K, int colour, int rhs) {
+  const int hw = (L.nx + 1) >> 1;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = t / hw;
+  int ti = t - row * hw;
+  int j = row % L.ny, k = row / L.ny;
+  if (k >= L.nz) return;
+  int i = 2 * ti + ((j + k + colour) & 1);
+  if (i >= L.nx) return;
+  int c = i + L.nx * (j + L.ny * k);
+  T f1, f2, f3;
+  cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, rhs != 0, f1, f2, f3);
+  cell_update<T, DIM, CORR>(L, K, c, i, j, k, f1, f2, f3);
+}
+
+// f_c += N_c(R u) on every cell (used when there is no pre-smoothing sweep to
+// carry it).
+template <typename T, int DIM, bool CORR>
 __global__ void __launch_bounds__(kBlock) k_coarse_rhs(Level<T> C, Coefs<T> K) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= C.ncell) return;
   int i, j, k;
   cell_ijk(q, C.nx, C.ny, i, j, k);
-  T n1, n2, n3;
-  apply_N<T, DIM>(C, K, q, i, j, k, n1, n2, n3);
-  C.fphi[q] += n1;
-  C.fmu[q] += n2;
-  C.fp[q] += n3;
+  T f1, f2, f3;
+  cell_rhs<T, DIM, CORR>(C, K, q, i, j, k, true, f1, f2, f3);
+}
+
+// ---------------------------------------------------------------- transfers
+
+// Residual and restriction, one thread per fine cell.  A warp covers a tile
+// of 16 x 2 (2D) or 8 x 2 x 2 (3D) fine cells, so the 2^d children of a
+// coarse cell sit in lanes l, l^1, l^16 (2D) or l, l^1, l^8, l^16 (3D) and are
+// summed by shuffles.  Writes u_c = R u (twice: the coarse iterate and u_c^0),
+// R phi_b in correction form, and f_c = R r (completed later by N_c(R u)).
+template <typename T, int DIM, bool CORR>
+__global__ void __launch_bounds__(kBlock) k_residual_restrict(Level<T> F, Level<T> C, Coefs<T> K) {
+  constexpr int TX = DIM == 3 ? 8 : 16;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int tiles_x = (F.nx + TX - 1) / TX;
+  const int tiles_y = F.ny >> 1;
+  const int tiles_z = DIM == 3 ? (F.nz >> 1) : 1;
+  if (warp >= tiles_x * tiles_y * tiles_z) return;  // whole warp
+  const int tx = warp % tiles_x;
+  const int rest = warp / tiles_x;
+  const int ty = rest % tiles_y, tz = rest / tiles_y;
+  const int i = tx * TX + (lane % TX);
+  const int j = 2 * ty + ((lane / TX) & 1);
+  const int k = DIM == 3 ? 2 * tz + (lane >> 4) : 0;
+  const bool valid = i < F.nx;
+  constexpr int NV = CORR ? 7 : 6;
+  T v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = T(0);
+  if (valid) {
+    int c = i + F.nx * (j + F.ny * k);
+    T n1, n2, n3;
+    eval_N<T, DIM, CORR>(F, K, F.phi, F.mu, F.p, c, i, j, k, n1, n2, n3);
+    v[0] = F.fphi[c] - n1;
+    v[1] = F.fmu[c] - n2;
+    v[2] = F.fp[c] - n3;
+    v[3] = F.phi[c];
+    v[4] = F.mu[c];
+    v[5] = F.p[c];
+    if (CORR) v[NV - 1] = F.phib[c];
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
+    v[q] += __shfl_xor_sync(0xffffffffu, v[q], TX);
+    if (DIM == 3) v[q] += __shfl_xor_sync(0xffffffffu, v[q], 16);
+  }
+  const bool leader = valid && (lane & 1) == 0 && ((lane / TX) & 1) == 0 && (DIM == 2 || lane < 16);
+  if (!leader) return;
+  const T w = DIM == 3 ? T(0.125) : T(0.25);
+  int q = (i >> 1) + C.nx * ((j >> 1) + C.ny * (k >> 1));
+  C.fphi[q] = w * v[0];
+  C.fmu[q] = w * v[1];
+  C.fp[q] = w * v[2];
+  C.phi[q] = C.phi0[q] = w * v[3];
+  C.mu[q] = C.mu0[q] = w * v[4];
+  C.p[q] = C.p0[q] = w * v[5];
+  if (CORR) C.phib[q] = w * v[NV - 1];
 }
 
 // u += P(u_c - u_c^0), P piecewise constant.
@@ -268,41 +427,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __syncthreads();
 }
 
-// Partial sums of r_phi^2 + r_mu^2 + (s r_p)^2 over the fine grid, one per block.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_resid_partial(Level<T> L, Coefs<T> K, double* partials) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
-  if (c < L.ncell) {
-    int i, j, k;
-    cell_ijk(c, L.nx, L.ny, i, j, k);
-    T n1, n2, n3;
-    apply_N<T, DIM>(L, K, c, i, j, k, n1, n2, n3);
-    double r1 = double(L.fphi[c] - n1), r2 = double(L.fmu[c] - n2);
-    double r3 = double(K.s) * double(L.fp[c] - n3);
-    acc[0] = r1 * r1 + r2 * r2 + r3 * r3;
-  }
-  block_sum<1>(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
-}
-
-// Sum the partials in a fixed order (deterministic), one block.
+// Sum the partials in a fixed order (deterministic), one block.  Loads go
+// through L2 (other blocks of this kernel may have just written them).
 template <int NV>
 __device__ __forceinline__ void sum_partials(const double* partials, int nparts, double (&tot)[NV]) {
   for (int q = 0; q < NV; ++q) tot[q] = 0.0;
   for (int b = threadIdx.x; b < nparts; b += blockDim.x)
-    for (int q = 0; q < NV; ++q) tot[q] += partials[b * NV + q];
+    for (int q = 0; q < NV; ++q) tot[q] += __ldcg(partials + b * NV + q);
   block_sum<NV>(tot);
 }
 
-// Finish the stopping norm.  mode 0: start of a step (records r0); mode 1:
-// after a V-cycle (counts it).  Sets the while-loop condition of the step graph.
-static __global__ void k_resid_finish(const double* partials, int nparts, int ncell, DevState* st,
-                               cudaGraphConditionalHandle cond, int mode, int use_cond) {
-  double tot[1];
-  sum_partials<1>(partials, nparts, tot);
-  if (threadIdx.x != 0) return;
-  double r = sqrt(tot[0] / ncell);
+// The loop decision after a norm r.  mode 0: start of a step (records r0);
+// mode 1: after a V-cycle (counts it).  Returns 1 while another cycle is due.
+__device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, int mode) {
   st->resid = r;
   unsigned int go = 0;
   if (st->failed == 0) {
@@ -322,6 +459,42 @@ static __global__ void k_resid_finish(const double* partials, int nparts, int nc
     }
   }
   st->go = (int)go;
+  return go;
+}
+
+// Stopping norm sqrt(mean over cells of r_phi^2 + r_mu^2 + (s r_p)^2) on the
+// finest grid, in one launch: every block writes its partial sum, and the
+// last block to finish (ticket counter) adds the partials in a fixed order and
+// takes the loop decision, setting the while-loop condition of the step graph.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double* partials, DevState* st,
+                                                 cudaGraphConditionalHandle cond, int mode, int use_cond) {
+  __shared__ bool last;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (c < L.ncell) {
+    int i, j, k;
+    cell_ijk(c, L.nx, L.ny, i, j, k);
+    T n1, n2, n3;
+    eval_N<T, DIM, false>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
+    double r1 = double(L.fphi[c] - n1), r2 = double(L.fmu[c] - n2);
+    double r3 = double(K.s) * double(L.fp[c] - n3);
+    acc[0] = r1 * r1 + r2 * r2 + r3 * r3;
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc[0];
+    __threadfence();
+    last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot[1];
+  sum_partials<1>(partials, gridDim.x, tot);
+  if (threadIdx.x != 0) return;
+  st->ticket = 0;
+  unsigned int go = loop_decision(st, sqrt(tot[0] / L.ncell), mode);
   if (use_cond) cudaGraphSetConditional(cond, go);
 }
 
@@ -385,12 +558,102 @@ static __global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, doub
   L.p[c] -= st->pmean;
 }
 
-// ---------------------------------------------------------------- coarsest
+// ---------------------------------------------------------------- coarse tail
 
-// The coarsest grid (2^d cells for power-of-two grids) solved in one block:
-// red-black sweeps until the residual has fallen by 1e-13 or stops falling.
+// The bottom of a V-cycle -- from some level down to the coarsest and back --
+// run by a single block.  On these small levels a kernel launch costs more
+// than the work, so the whole tail is one launch with block barriers between
+// passes.  Global memory written by the block is visible to it after
+// __syncthreads.
+template <typename T>
+struct Tail {
+  Level<T> lev[kTailMaxLevels];
+  int n;        // levels in the tail; the last one is the coarsest
+  int nu1, nu2;
+  int top_rhs;  // complete the FAS right-hand side of the tail's top level first
+};
+
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void tail_smooth(const Level<T>& L, const Coefs<T>& K, int colour, bool rhs) {
+  const int hw = (L.nx + 1) >> 1;
+  const int total = hw * L.ny * L.nz;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int row = t / hw;
+    int ti = t - row * hw;
+    int j = row % L.ny, k = row / L.ny;
+    int i = 2 * ti + ((j + k + colour) & 1);
+    if (i >= L.nx) continue;
+    int c = i + L.nx * (j + L.ny * k);
+    T f1, f2, f3;
+    cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, rhs, f1, f2, f3);
+    cell_update<T, DIM, CORR>(L, K, c, i, j, k, f1, f2, f3);
+  }
+  __syncthreads();
+}
+
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void tail_rhs(const Level<T>& L, const Coefs<T>& K) {
+  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+    int i, j, k;
+    cell_ijk(c, L.nx, L.ny, i, j, k);
+    T f1, f2, f3;
+    cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, true, f1, f2, f3);
+  }
+  __syncthreads();
+}
+
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void tail_restrict(const Level<T>& F, const Level<T>& C, const Coefs<T>& K) {
+  const T w = DIM == 3 ? T(0.125) : T(0.25);
+  const int kz = DIM == 3 ? 2 : 1;
+  for (int q = threadIdx.x; q < C.ncell; q += blockDim.x) {
+    int I, J, KK;
+    cell_ijk(q, C.nx, C.ny, I, J, KK);
+    T r1 = 0, r2 = 0, r3 = 0, a = 0, b = 0, d = 0, e = 0;
+    for (int dk = 0; dk < kz; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          int i = 2 * I + di, j = 2 * J + dj, k = 2 * KK + dk;
+          int c = i + F.nx * (j + F.ny * k);
+          T n1, n2, n3;
+          eval_N<T, DIM, CORR>(F, K, F.phi, F.mu, F.p, c, i, j, k, n1, n2, n3);
+          r1 += F.fphi[c] - n1;
+          r2 += F.fmu[c] - n2;
+          r3 += F.fp[c] - n3;
+          a += F.phi[c];
+          b += F.mu[c];
+          d += F.p[c];
+          if (CORR) e += F.phib[c];
+        }
+    C.fphi[q] = w * r1;
+    C.fmu[q] = w * r2;
+    C.fp[q] = w * r3;
+    C.phi[q] = C.phi0[q] = w * a;
+    C.mu[q] = C.mu0[q] = w * b;
+    C.p[q] = C.p0[q] = w * d;
+    if (CORR) C.phib[q] = w * e;
+  }
+  __syncthreads();
+}
+
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_coarsest(Level<T> L, Coefs<T> K) {
+__device__ __forceinline__ void tail_prolong(const Level<T>& F, const Level<T>& C) {
+  for (int c = threadIdx.x; c < F.ncell; c += blockDim.x) {
+    int i, j, k;
+    cell_ijk(c, F.nx, F.ny, i, j, k);
+    int q = (i >> 1) + C.nx * ((j >> 1) + C.ny * (DIM == 3 ? (k >> 1) : 0));
+    F.phi[c] += C.phi[q] - C.phi0[q];
+    F.mu[c] += C.mu[q] - C.mu0[q];
+    F.p[c] += C.p[q] - C.p0[q];
+  }
+  __syncthreads();
+}
+
+// The coarsest grid: red-black sweeps until the residual has fallen by 1e-13,
+// or falls by less than 10% in a sweep (the arithmetic's floor), or after
+// 2000 sweeps.
+template <typename T, int DIM, bool CORR>
+__device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>& K) {
   __shared__ double sh_r;
   double r0 = -1.0, prev = 0.0;
   for (int it = 0; it <= 2000; ++it) {
@@ -399,7 +662,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsest(Level<T> L, Coefs<T> K) {
       int i, j, k;
       cell_ijk(c, L.nx, L.ny, i, j, k);
       T n1, n2, n3;
-      apply_N<T, DIM>(L, K, c, i, j, k, n1, n2, n3);
+      eval_N<T, DIM, CORR>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
       double r1 = double(L.fphi[c] - n1), r2 = double(L.fmu[c] - n2);
       double r3 = double(K.s) * double(L.fp[c] - n3);
       acc[0] += r1 * r1 + r2 * r2 + r3 * r3;
@@ -411,34 +674,32 @@ __global__ void __launch_bounds__(kBlock) k_coarsest(Level<T> L, Coefs<T> K) {
     __syncthreads();
     if (r0 < 0.0) r0 = r;
     if (!(r > 1e-13 * r0) || r < 1e-300) break;
-    if (it > 50 && r > 0.999 * prev) break;
+    if (it > 0 && r > 0.9 * prev) break;
     prev = r;
-    for (int colour = 0; colour < 2; ++colour) {
-      for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
-        int i, j, k;
-        cell_ijk(c, L.nx, L.ny, i, j, k);
-        if (((i + j + k) & 1) != colour) continue;
-        T phic = L.phi[c], muc = L.mu[c], pc = L.p[c], phimc = L.phim[c];
-        Sums<T> S;
-        face_sums<T, DIM>(L, K, c, i, j, k, phic, muc, pc, L.phis[c], S);
-        T n1 = phic - K.s * L.ih2 * (S.Mdmu + S.adp);
-        T n2 = muc - chi(phic, phimc) + K.e34 * L.ih2 * S.dphi;
-        T n3 = -L.ih2 * (S.dp + K.gamma * S.admu);
-        T R1 = L.fphi[c] - n1, R2 = L.fmu[c] - n2, R3 = L.fp[c] - n3;
-        T inv_m = T(1) / T(S.m);
-        T Ae = K.s * L.ih2 * (S.M - K.gamma * S.a * S.a * inv_m);
-        T CD = K.s * S.a * inv_m;
-        T G = K.gamma * L.ih2 * S.a;
-        T B = dchi_da(phic, phimc) + K.e34 * L.ih2 * T(S.m);
-        T dphi = (R1 - Ae * R2 - CD * R3) / (T(1) + Ae * B);
-        T dmu = R2 + B * dphi;
-        T dp = (R3 - G * dmu) * inv_m / L.ih2;
-        L.phi[c] = phic + dphi;
-        L.mu[c] = muc + dmu;
-        L.p[c] = pc + dp;
-      }
-      __syncthreads();
+    for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(L, K, colour, false);
+  }
+}
+
+template <typename T, int DIM, bool CORR>
+__global__ void __launch_bounds__(kTailThreads) k_tail(Tail<T> tl, Coefs<T> K) {
+  const int n = tl.n;
+  for (int l = 0; l + 1 < n; ++l) {
+    const Level<T>& L = tl.lev[l];
+    bool rhs = l > 0 || tl.top_rhs;
+    if (rhs && tl.nu1 == 0) {
+      tail_rhs<T, DIM, CORR>(L, K);
+      rhs = false;
     }
+    for (int it = 0; it < tl.nu1; ++it)
+      for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(L, K, colour, rhs && it == 0);
+    tail_restrict<T, DIM, CORR>(L, tl.lev[l + 1], K);
+  }
+  if (n > 1 || tl.top_rhs) tail_rhs<T, DIM, CORR>(tl.lev[n - 1], K);
+  coarsest_solve<T, DIM, CORR>(tl.lev[n - 1], K);
+  for (int l = n - 2; l >= 0; --l) {
+    tail_prolong<T, DIM>(tl.lev[l], tl.lev[l + 1]);
+    for (int it = 0; it < tl.nu2; ++it)
+      for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(tl.lev[l], K, colour, false);
   }
 }
 
