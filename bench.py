@@ -243,6 +243,25 @@ def barrier(world):
         dist.barrier()
 
 
+def time_steps(run, steps, stream, flush):
+    """K steps, each preceded by an untimed L2 flush and bracketed by CUDA
+    events on the solver's stream; returns (device ms, V-cycles, last norm)."""
+    import torch
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    vtot, resid = 0, None
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        ev0[k].record(stream)
+        run.step_async(1)
+        ev1[k].record(stream)
+        _, v, resid = run.wait()
+        vtot += v
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), vtot, resid
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -268,23 +287,12 @@ def run_ours(args):
     run.step(args.warmup)
     state0 = run.get_state()  # the e2e leg below replays the same K steps
     # timed region: K steps, L2 flushed before each, device time by events
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    vtot = 0
     barrier(world)
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-        ev0[k].record(stream)
-        run.step_async(1)
-        ev1[k].record(stream)
-        _, v, resid = run.wait()
-        vtot += v
+    dev_ms, vtot, resid = time_steps(run, args.steps, stream, flush)
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop() if sampler else None
-    dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     max_ms = reduce_max(dev_ms, world)
     units = reduce_sum(float(ncell * args.steps), world)
     value = units / (max_ms / 1e3)
@@ -329,6 +337,25 @@ def run_ours(args):
     if dom != "smooth":
         roofline["note"] = "largest device-time share this run: %s" % dom
 
+    # the mixed-precision form on the same workload and steps, timed the same way
+    run32 = chhs.Run(shape, w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream,
+                     opts=chhs.default_opts(precision=1))
+    run32.set_state(*state0)
+    run32.step(args.warmup)
+    run32.set_state(*state0)
+    barrier(world)
+    torch.cuda.synchronize()
+    mx_ms, mx_v, mx_resid = time_steps(run32, args.steps, stream, flush)
+    mx_max = reduce_max(mx_ms, world)
+    run.set_state(*state0)
+    run.step(args.steps)
+    diff = float(np.max(np.abs(run.get_phi() - run32.get_phi())))
+    mixed = {"value": units / (mx_max / 1e3), "unit": UNIT, "ms_per_step": mx_max / args.steps,
+             "vcycles_per_step": mx_v / args.steps, "final_resid": mx_resid,
+             "dtype": "f32 V-cycles, f64 residual/update/norms",
+             "max_abs_phi_diff_vs_f64_after_K_steps": diff}
+    run32.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, nsteps, secs = oracle_rate(w)
@@ -341,7 +368,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config(world), "vcycles_per_step": vtot / args.steps, "final_resid": resid,
-                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "mixed": mixed, "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

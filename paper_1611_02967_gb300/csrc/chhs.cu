@@ -53,24 +53,29 @@ std::vector<Shape> level_shapes(int dim, const int n[3], int coarsest) {
   return out;
 }
 
-// phi mu p fphi fmu fp phim phis phi0 mu0 p0, ax ay Mx My, sM sa, cAe cCD cG (+ az Mz in 3D)
+// Per-level fields: phi mu p fphi fmu fp phim phis phi0 mu0 p0, ax ay Mx My,
+// sM sa, cAe cCD cG (+ az Mz in 3D), and in single precision also phi_b.
 constexpr int kBaseFields = 11;
-int level_fields(int dim) { return kBaseFields + (dim == 3 ? 11 : 9); }
+int level_fields(int dim, bool single) { return kBaseFields + (dim == 3 ? 11 : 9) + (single ? 1 : 0); }
 
 // Levels with at most this many cells run inside the one-block tail kernel.
 // In double precision one SM does 2 FMA per clock, so only the tiniest levels
-// (8 x 8, 4 x 4 x 4) are cheaper there than as grid-wide launches.
+// (8 x 8, 4 x 4 x 4) are cheaper there than as grid-wide launches; in single
+// precision (64x the rate) levels up to 32 x 32 are.
 constexpr int kTailCellsF64 = 64;
+constexpr int kTailCellsF32 = 1024;
 
 struct Layout {
   std::vector<Shape> shapes;
   size_t state_off, partial_off, phimm1_off;
-  std::vector<size_t> level_off;  // start of each level's field arrays
+  int nlev64;                       // double-precision levels (all, or the finest only when mixed)
+  std::vector<size_t> level_off;    // start of each double-precision level's arrays
+  std::vector<size_t> level32_off;  // start of each single-precision level's arrays (mixed only)
   size_t total;
   int nparts;  // partial-sum slots (blocks of the finest grid)
 };
 
-Layout make_layout(int dim, const int n[3], int coarsest) {
+Layout make_layout(int dim, const int n[3], int coarsest, int precision) {
   Layout L;
   L.shapes = level_shapes(dim, n, coarsest);
   size_t off = 0;
@@ -82,18 +87,26 @@ Layout make_layout(int dim, const int n[3], int coarsest) {
   off += align_up(sizeof(double) * 6 * (size_t)L.nparts);
   L.phimm1_off = off;
   off += align_up(sizeof(double) * (size_t)nf);
-  for (const Shape& s : L.shapes) {
+  L.nlev64 = precision == 1 ? 1 : (int)L.shapes.size();
+  for (int l = 0; l < L.nlev64; ++l) {
+    const Shape& s = L.shapes[l];
     size_t nc = (size_t)s.n[0] * s.n[1] * s.n[2];
     L.level_off.push_back(off);
-    off += level_fields(dim) * align_up(sizeof(double) * nc);
+    off += level_fields(dim, false) * align_up(sizeof(double) * nc);
   }
+  if (precision == 1)
+    for (const Shape& s : L.shapes) {
+      size_t nc = (size_t)s.n[0] * s.n[1] * s.n[2];
+      L.level32_off.push_back(off);
+      off += level_fields(dim, true) * align_up(sizeof(float) * nc);
+    }
   L.total = off;
   return L;
 }
 
 bool valid_opts(const chhs_opts& o) {
   return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.max_v >= 1 && o.coarsest >= 1 &&
-         o.tol > 0 && (o.precision == 0);
+         o.tol > 0 && (o.precision == 0 || o.precision == 1);
 }
 
 bool valid_problem(int dim, const int n[3], double h, double eps, double gamma, double dt) {
@@ -140,9 +153,11 @@ struct chhs {
   bool own_arena = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  std::vector<Level<double>> lev;
-  int tail_start = 0;   // first level run by the one-block tail kernel
-  Tail<double> tail{};  // its levels
+  std::vector<Level<double>> lev;   // double precision: all levels, or the finest only when mixed
+  std::vector<Level<float>> lev32;  // single-precision correction hierarchy (mixed precision)
+  int tail_start = 0;               // first level run by the one-block tail kernel
+  Tail<double> tail{};              // its levels (double-precision V-cycles)
+  Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
   DevState* st = nullptr;
   double* partials = nullptr;
@@ -188,7 +203,8 @@ void launch(chhs_t* run, cudaStream_t s, int kind, double units, F&& f) {
 }
 
 // Cells of colour 0 ((i+j+k) even) in a box whose corner cell is even.
-double colour_cells(const Level<double>& L, int colour) {
+template <typename T>
+double colour_cells(const Level<T>& L, int colour) {
   double n = L.ncell;
   bool odd = (L.ncell & 1) != 0;
   return colour == 0 ? (odd ? (n + 1) / 2 : n / 2) : (odd ? (n - 1) / 2 : n / 2);
@@ -196,61 +212,88 @@ double colour_cells(const Level<double>& L, int colour) {
 
 template <int DIM>
 struct Enqueue {
-  static Coefs<double> coefs(const chhs_t* run) {
-    return Coefs<double>{run->dt, run->gamma, 0.75 * run->eps * run->eps};
+  template <typename T>
+  static Coefs<T> coefs(const chhs_t* run) {
+    return Coefs<T>{T(run->dt), T(run->gamma), T(0.75 * run->eps * run->eps)};
   }
 
   // sweeps red-black sweeps; with rhs the first one also completes the FAS
   // right-hand side of this (coarse) level.
-  static void smooth(chhs_t* run, cudaStream_t s, const Level<double>& L, int sweeps, bool rhs) {
-    const Coefs<double> K = coefs(run);
+  template <typename T, bool CORR>
+  static void smooth(chhs_t* run, cudaStream_t s, const Level<T>& L, int sweeps, bool rhs) {
+    const Coefs<T> K = coefs<T>(run);
     const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
     const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
     for (int it = 0; it < sweeps; ++it)
       for (int colour = 0; colour < 2; ++colour) {
         const int with_rhs = (rhs && it == 0) ? 1 : 0;
         launch(run, s, CHHS_K_SMOOTH, colour_cells(L, colour), [&] {
-          k_smooth<double, DIM, false><<<blocks, kSmoothBlock, 0, s>>>(L, K, colour, with_rhs);
+          k_smooth<T, DIM, CORR><<<blocks, kSmoothBlock, 0, s>>>(L, K, colour, with_rhs);
         });
       }
   }
 
-  static void vcycle(chhs_t* run, cudaStream_t s, int l) {
-    const Coefs<double> K = coefs(run);
-    const Level<double>& L = run->lev[l];
+  // One FAS V(nu1, nu2)-cycle from level l down, on a hierarchy of either precision.
+  template <typename T, bool CORR>
+  static void vcycle(chhs_t* run, cudaStream_t s, const std::vector<Level<T>>& lev, const Tail<T>& tail,
+                     int l) {
+    const Coefs<T> K = coefs<T>(run);
+    const Level<T>& L = lev[l];
     if (l == run->tail_start) {
       launch(run, s, CHHS_K_COARSEST, 1.0, [&] {
-        k_tail<double, DIM, false><<<1, kTailThreads, 0, s>>>(run->tail, K);
+        k_tail<T, DIM, CORR><<<1, kTailThreads, 0, s>>>(tail, K);
       });
       return;
     }
-    const Level<double>& C = run->lev[l + 1];
+    const Level<T>& C = lev[l + 1];
     const bool rhs = l > 0;
     if (rhs && run->opts.nu1 == 0)
       launch(run, s, CHHS_K_COARSE_RHS, L.ncell, [&] {
-        k_coarse_rhs<double, DIM, false><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K);
+        k_coarse_rhs<T, DIM, CORR><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K);
       });
-    smooth(run, s, L, run->opts.nu1, rhs && run->opts.nu1 > 0);
+    smooth<T, CORR>(run, s, L, run->opts.nu1, rhs && run->opts.nu1 > 0);
     constexpr int TX = DIM == 3 ? 8 : 16;
     const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
     const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
     launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
-      k_residual_restrict<double, DIM, false><<<rblocks, kBlock, 0, s>>>(L, C, K);
+      k_residual_restrict<T, DIM, CORR><<<rblocks, kBlock, 0, s>>>(L, C, K);
     });
-    vcycle(run, s, l + 1);
+    vcycle<T, CORR>(run, s, lev, tail, l + 1);
     launch(run, s, CHHS_K_PROLONG, L.ncell, [&] {
-      k_prolong<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, C);
+      k_prolong<T, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, C);
     });
-    smooth(run, s, L, run->opts.nu2, false);
+    smooth<T, CORR>(run, s, L, run->opts.nu2, false);
   }
 
+  static bool mixed(const chhs_t* run) { return run->opts.precision == 1; }
+
+  // The stopping norm (and, when mixed, the next inner solve's right-hand side).
   static void norm(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int mode, int use_cond) {
-    const Coefs<double> K = coefs(run);
+    const Coefs<double> K = coefs<double>(run);
     const Level<double>& L = run->lev[0];
     launch(run, s, CHHS_K_NORM, L.ncell, [&] {
-      k_norm<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K, run->partials, run->st, cond, mode,
-                                                              use_cond);
+      if (mixed(run))
+        k_norm_mixed<DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K, run->lev32[0], run->partials, run->st,
+                                                              cond, mode, use_cond);
+      else
+        k_norm<double, DIM><<<nblocks(L.ncell), kBlock, 0, s>>>(L, K, run->partials, run->st, cond, mode,
+                                                                use_cond);
     });
+  }
+
+  // One iteration of the step's loop: a double-precision V-cycle, or a
+  // single-precision correction V-cycle and the double-precision update.
+  static void iteration(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+    if (mixed(run)) {
+      vcycle<float, true>(run, s, run->lev32, run->tail32, 0);
+      const Level<double>& L = run->lev[0];
+      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+        k_mixed_update<<<nblocks(L.ncell), kBlock, 0, s>>>(L, run->lev32[0]);
+      });
+    } else {
+      vcycle<double, false>(run, s, run->lev, run->tail, 0);
+    }
+    norm(run, s, cond, 1, use_cond);
   }
 
   static void frame_head(chhs_t* run, cudaStream_t s) {
@@ -263,10 +306,22 @@ struct Enqueue {
         k_restrict_coef<double, DIM><<<nblocks(run->lev[l].ncell), kBlock, 0, s>>>(run->lev[l - 1],
                                                                                   run->lev[l]);
       });
-    const Coefs<double> K = coefs(run);
+    const Coefs<double> K = coefs<double>(run);
     for (size_t l = 0; l < run->lev.size(); ++l)
       launch(run, s, CHHS_K_FRAME, 1.0, [&] {
         k_coef<double, DIM><<<nblocks(run->lev[l].ncell), kBlock, 0, s>>>(run->lev[l], K);
+      });
+    if (!mixed(run)) return;
+    const std::vector<Level<float>>& G = run->lev32;
+    launch(run, s, CHHS_K_FRAME, 1.0, [&] { k_to_f32<DIM><<<nblocks(F.ncell), kBlock, 0, s>>>(F, G[0]); });
+    for (size_t l = 1; l < G.size(); ++l)
+      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+        k_restrict_coef<float, DIM><<<nblocks(G[l].ncell), kBlock, 0, s>>>(G[l - 1], G[l]);
+      });
+    const Coefs<float> K32 = coefs<float>(run);
+    for (size_t l = 0; l < G.size(); ++l)
+      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+        k_coef<float, DIM><<<nblocks(G[l].ncell), kBlock, 0, s>>>(G[l], K32);
       });
   }
 
@@ -310,8 +365,7 @@ struct Enqueue {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     run->counter = &n_v;
-    vcycle(run, cs2, 0);
-    norm(run, cs2, cond, 1, 1);
+    iteration(run, cs2, cond, 1);
     CU(cudaStreamEndCapture(cs2, &body));
     run->counter = &n_frame;
     frame_tail(run, cs);
@@ -334,8 +388,7 @@ struct Enqueue {
       CU(cudaMemcpyAsync(run->host_st, run->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       if (!run->host_st->go) break;
-      vcycle(run, s, 0);
-      norm(run, s, 0, 1, 0);
+      iteration(run, s, 0, 0);
     }
     frame_tail(run, s);
     CU(cudaGetLastError());
@@ -364,50 +417,63 @@ __global__ void k_reset_call(DevState* st, double tol, int max_v) {
   st->max_v = max_v;
 }
 
+// The arrays of one level, carved out of the arena at base.
+template <typename T>
+Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool single) {
+  size_t nc = (size_t)sh.n[0] * sh.n[1] * sh.n[2];
+  size_t stride = align_up(sizeof(T) * nc);
+  const int nf = level_fields(run->dim, single);
+  T* f[kBaseFields + 12];
+  for (int q = 0; q < nf; ++q) f[q] = reinterpret_cast<T*>(base + q * stride);
+  const double hl = run->h * double(1 << l);
+  Level<T> L;
+  L.phi = f[0]; L.mu = f[1]; L.p = f[2];
+  L.fphi = f[3]; L.fmu = f[4]; L.fp = f[5];
+  L.phim = f[6]; L.phis = f[7];
+  L.phi0 = f[8]; L.mu0 = f[9]; L.p0 = f[10];
+  L.ax = f[11]; L.ay = f[12]; L.Mx = f[13]; L.My = f[14];
+  L.sM = f[15]; L.sa = f[16];
+  L.cAe = f[17]; L.cCD = f[18]; L.cG = f[19];
+  int q = 20;
+  L.az = run->dim == 3 ? f[q++] : nullptr;
+  L.Mz = run->dim == 3 ? f[q++] : nullptr;
+  L.phib = single ? f[q++] : nullptr;
+  L.nx = sh.n[0]; L.ny = sh.n[1]; L.nz = sh.n[2];
+  L.ncell = (int)nc;
+  L.ih2 = T(1.0 / (hl * hl));
+  L.h2 = T(hl * hl);
+  L.sih2 = T(run->dt / (hl * hl));
+  L.e34ih2 = T(0.75 * run->eps * run->eps / (hl * hl));
+  return L;
+}
+
+template <typename T>
+void fill_tail(Tail<T>& tail, const std::vector<Level<T>>& lev, int start, const chhs_opts& o) {
+  tail.n = 0;
+  for (int l = start; l < (int)lev.size(); ++l) tail.lev[tail.n++] = lev[l];
+  tail.nu1 = o.nu1;
+  tail.nu2 = o.nu2;
+  tail.top_rhs = start > 0 ? 1 : 0;
+}
+
 chhs_status setup_handle(chhs_t* run) {
   const Layout& Lo = run->layout;
   run->st = reinterpret_cast<DevState*>(run->arena + Lo.state_off);
   run->partials = reinterpret_cast<double*>(run->arena + Lo.partial_off);
   run->phimm1 = reinterpret_cast<double*>(run->arena + Lo.phimm1_off);
-  double hl = run->h;
-  for (size_t l = 0; l < Lo.shapes.size(); ++l) {
-    const Shape& s = Lo.shapes[l];
-    size_t nc = (size_t)s.n[0] * s.n[1] * s.n[2];
-    size_t stride = align_up(sizeof(double) * nc);
-    char* base = run->arena + Lo.level_off[l];
-    const int nf = level_fields(run->dim);
-    double* f[kBaseFields + 11];
-    for (int q = 0; q < nf; ++q) f[q] = reinterpret_cast<double*>(base + q * stride);
-    Level<double> L;
-    L.phi = f[0]; L.mu = f[1]; L.p = f[2];
-    L.fphi = f[3]; L.fmu = f[4]; L.fp = f[5];
-    L.phim = f[6]; L.phis = f[7];
-    L.phi0 = f[8]; L.mu0 = f[9]; L.p0 = f[10];
-    L.ax = f[11]; L.ay = f[12]; L.Mx = f[13]; L.My = f[14];
-    L.sM = f[15]; L.sa = f[16];
-    L.cAe = f[17]; L.cCD = f[18]; L.cG = f[19];
-    L.az = run->dim == 3 ? f[20] : nullptr;
-    L.Mz = run->dim == 3 ? f[21] : nullptr;
-    L.phib = nullptr;
-    L.nx = s.n[0]; L.ny = s.n[1]; L.nz = s.n[2];
-    L.ncell = (int)nc;
-    L.ih2 = 1.0 / (hl * hl);
-    L.h2 = hl * hl;
-    L.sih2 = run->dt * L.ih2;
-    L.e34ih2 = 0.75 * run->eps * run->eps * L.ih2;
-    run->lev.push_back(L);
-    hl *= 2.0;
-  }
-  const int nl = (int)run->lev.size();
+  for (int l = 0; l < Lo.nlev64; ++l)
+    run->lev.push_back(make_level<double>(run, Lo.shapes[l], l, run->arena + Lo.level_off[l], false));
+  for (size_t l = 0; l < Lo.level32_off.size(); ++l)
+    run->lev32.push_back(make_level<float>(run, Lo.shapes[l], (int)l, run->arena + Lo.level32_off[l], true));
+  const int nl = (int)Lo.shapes.size();
+  const int tail_cells = run->opts.precision == 1 ? kTailCellsF32 : kTailCellsF64;
   run->tail_start = nl - 1;
-  while (run->tail_start > 0 && run->lev[run->tail_start - 1].ncell <= kTailCellsF64 &&
+  while (run->tail_start > 0 && Lo.shapes[run->tail_start - 1].n[0] * Lo.shapes[run->tail_start - 1].n[1] *
+                                        Lo.shapes[run->tail_start - 1].n[2] <= tail_cells &&
          nl - (run->tail_start - 1) <= kTailMaxLevels)
     --run->tail_start;
-  run->tail.n = nl - run->tail_start;
-  for (int l = run->tail_start; l < nl; ++l) run->tail.lev[l - run->tail_start] = run->lev[l];
-  run->tail.nu1 = run->opts.nu1;
-  run->tail.nu2 = run->opts.nu2;
-  run->tail.top_rhs = run->tail_start > 0 ? 1 : 0;
+  fill_tail(run->tail, run->lev, run->tail_start, run->opts);
+  fill_tail(run->tail32, run->lev32, run->tail_start, run->opts);
   CU(cudaMemsetAsync(run->arena, 0, Lo.total, run->stream));
   CU(cudaMallocHost(&run->host_st, sizeof(DevState)));
   memset(run->host_st, 0, sizeof(DevState));
@@ -432,7 +498,7 @@ chhs_status create_impl(int dim, const int n[3], double h, double eps, double ga
   for (int a = 0; a < 3; ++a) run->n[a] = (a < dim) ? n[a] : 1;
   run->h = h; run->eps = eps; run->gamma = gamma; run->dt = dt;
   run->opts = o;
-  run->layout = make_layout(dim, run->n, o.coarsest);
+  run->layout = make_layout(dim, run->n, o.coarsest, o.precision);
   chhs_status s = CHHS_OK;
   if (cuda_stream) {
     run->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -502,7 +568,7 @@ size_t chhs_workspace_bytes(int dim, const int n[3], const chhs_opts* opts) {
   if (opts) o = *opts;
   if (!valid_problem(dim, n, 1.0, 1.0, 0.0, 1.0) || !valid_opts(o)) return 0;
   int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
-  return make_layout(dim, nn, o.coarsest).total;
+  return make_layout(dim, nn, o.coarsest, o.precision).total;
 }
 
 chhs_status chhs_create(int dim, const int n[3], double h, double eps, double gamma, double dt,

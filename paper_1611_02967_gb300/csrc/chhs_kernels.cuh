@@ -498,6 +498,77 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
   if (use_cond) cudaGraphSetConditional(cond, go);
 }
 
+// ---------------------------------------------------------------- mixed precision
+//
+// Defect correction (iterative refinement): with u the double-precision
+// iterate on the finest grid, r = f - N(u) is formed in double; the
+// correction e solves N(u + e) - N(u) = r, which single-precision FAS
+// V-cycles approximate in correction form (base phi_b = u's phi rounded to
+// single); then u <- u + e in double.  Every rounding error of the inner
+// solve is relative to the correction, not to u, so the outer loop reaches
+// the double-precision tolerance.
+
+// phi^m and phi* of the finest grid in single precision (once per step).
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_to_f32(Level<double> F, Level<float> G) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= F.ncell) return;
+  G.phim[c] = (float)F.phim[c];
+  G.phis[c] = (float)F.phis[c];
+}
+
+// The stopping norm of the double-precision iterate, as k_norm, and the
+// right-hand side of the next inner solve: f32 = r rounded, e = 0,
+// phi_b = phi rounded.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<double> K, Level<float> G,
+                                                       double* partials, DevState* st,
+                                                       cudaGraphConditionalHandle cond, int mode, int use_cond) {
+  __shared__ bool last;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (c < L.ncell) {
+    int i, j, k;
+    cell_ijk(c, L.nx, L.ny, i, j, k);
+    double n1, n2, n3;
+    eval_N<double, DIM, false>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
+    double r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = L.fp[c] - n3;
+    double r3s = K.s * r3;
+    acc[0] = r1 * r1 + r2 * r2 + r3s * r3s;
+    G.fphi[c] = (float)r1;
+    G.fmu[c] = (float)r2;
+    G.fp[c] = (float)r3;
+    G.phi[c] = 0.f;
+    G.mu[c] = 0.f;
+    G.p[c] = 0.f;
+    G.phib[c] = (float)L.phi[c];
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc[0];
+    __threadfence();
+    last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot[1];
+  sum_partials<1>(partials, gridDim.x, tot);
+  if (threadIdx.x != 0) return;
+  st->ticket = 0;
+  unsigned int go = loop_decision(st, sqrt(tot[0] / L.ncell), mode);
+  if (use_cond) cudaGraphSetConditional(cond, go);
+}
+
+// u <- u + e in double precision.
+static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L, Level<float> G) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.ncell) return;
+  L.phi[c] += (double)G.phi[c];
+  L.mu[c] += (double)G.mu[c];
+  L.p[c] += (double)G.p[c];
+}
+
 // ---------------------------------------------------------------- step frame
 
 // phi* = 3/2 phi^m - 1/2 phi^{m-1} (Eq. 2.4); f_phi = phi^m;

@@ -4,8 +4,10 @@ The red-black GPU smoother and the lexicographic oracle walk different
 iterates to the same unique solution of (2.5)-(2.7) (Theorem 2.1), so every
 comparison is on converged steps from identical inputs: the GPU's own
 (phi^m, phi^{m-1}) are handed to the oracle, which solves that one step to
-1e-13, and the GPU's phi^{m+1} must agree within 1e-9 (double-precision path).
-mu is compared too; p is compared modulo its constant (pure Neumann).
+1e-13, and the GPU's phi^{m+1} must agree within 1e-9 for the double-precision
+path and within 1e-8 for the mixed-precision path (single-precision V-cycles
+inside a double-precision defect-correction loop).  mu is compared too; p is
+compared modulo its constant (pure Neumann).
 """
 import numpy as np
 import pytest
@@ -15,14 +17,19 @@ from paper_1611_02967_gb300 import chhs, inputs
 
 pytestmark = pytest.mark.gpu
 
-PHI_TOL = 1e-9
+PHI_TOL = {0: 1e-9, 1: 1e-8}  # by precision mode
+PRECISIONS = [0, 1]
 
 
 def _oracle_prm(h, eps, gamma, dt):
     return oracle.Params(h, eps, gamma, dt, tol=1e-13, max_v=100)
 
 
-def _check_step(run, h, eps, gamma, dt, tol_phi=PHI_TOL):
+def _run(shape, h, eps, gamma, dt, precision, **kw):
+    return chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=precision, **kw))
+
+
+def _check_step(run, h, eps, gamma, dt, tol_phi):
     """Take one GPU step from the run's current state and compare it with the oracle."""
     phim, phimm1, mu_prev, p_prev = run.get_state()
     run.step(1)
@@ -40,6 +47,7 @@ def _check_step(run, h, eps, gamma, dt, tol_phi=PHI_TOL):
     return dphi
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("shape,h,eps,gamma,dt", [
     ((16, 16), 0.2, 0.1, 2.0, 0.02),
     ((24, 40), 0.1, 0.08, 1.0, 0.01),      # ragged: 960 cells, coarsens to 3 x 5
@@ -48,53 +56,57 @@ def _check_step(run, h, eps, gamma, dt, tol_phi=PHI_TOL):
     ((8, 8, 8), 0.2, 0.1, 2.0, 0.01),
     ((16, 8, 12), 0.1, 0.08, 4.0, 0.005),  # 3D, uneven
 ])
-def test_single_steps_match_oracle(shape, h, eps, gamma, dt):
+def test_single_steps_match_oracle(shape, h, eps, gamma, dt, precision):
     phi0 = inputs.spinodal(shape, 101, mean=0.0, amplitude=0.5)
-    with chhs.Run(shape, h, eps, gamma, dt) as run:
+    with _run(shape, h, eps, gamma, dt, precision) as run:
         run.set_phi(phi0)
         for _ in range(3):
-            _check_step(run, h, eps, gamma, dt)
+            _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
 
 
-def test_spinodal64_every_step():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_spinodal64_every_step(precision):
     """The 64x64 spinodal workload (eps 0.05, gamma 1, dt 0.01, 50 steps): every step."""
     w = inputs.workload("spinodal64")
-    with chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"]) as run:
+    with _run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], precision) as run:
         run.set_phi(w["phi0"])
         worst = 0.0
         for k in range(w["steps"]):
-            worst = max(worst, _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"]))
-        print("spinodal64 worst max|dphi| over 50 steps: %.3e" % worst)
+            worst = max(worst, _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"], PHI_TOL[precision]))
+        print("spinodal64 precision %d worst max|dphi| over 50 steps: %.3e" % (precision, worst))
 
 
-def test_spinodal512_sampled_steps():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_spinodal512_sampled_steps(precision):
     """The 512x512 workload at full size, steps sampled across the run (oracle one step each)."""
     w = inputs.workload("spinodal512")
-    with chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"]) as run:
+    with _run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], precision) as run:
         run.set_phi(w["phi0"])
         done = 0
         for target in (0, 40, 120):
             if target > done:
                 run.step(target - done)
                 done = target
-            _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"])
+            _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"], PHI_TOL[precision])
             done += 1
 
 
-def test_bubbles128_one_step():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_bubbles128_one_step(precision):
     """The 128^3 bubble workload at full size: the first step and a later one."""
     w = inputs.workload("bubbles128")
-    with chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"]) as run:
+    with _run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], precision) as run:
         run.set_phi(w["phi0"])
-        _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"])
+        _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"], PHI_TOL[precision])
         run.step(5)
-        _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"])
+        _check_step(run, w["h"], w["eps"], w["gamma"], w["dt"], PHI_TOL[precision])
 
 
-def test_mass_energy_match_oracle_and_invariants():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_mass_energy_match_oracle_and_invariants(precision):
     w = inputs.workload("spinodal64")
     h, eps = w["h"], w["eps"]
-    with chhs.Run(w["shape"], h, eps, w["gamma"], w["dt"]) as run:
+    with _run(w["shape"], h, eps, w["gamma"], w["dt"], precision) as run:
         run.set_phi(w["phi0"])
         m0 = run.mass()
         assert abs(m0 - oracle.mass(w["phi0"], h)) < 1e-13
@@ -112,6 +124,21 @@ def test_mass_energy_match_oracle_and_invariants():
             if F_prev is not None:
                 assert F <= F_prev + 1e-12
             F_prev = F
+
+
+def test_mixed_matches_double_on_the_gpu():
+    """Both GPU forms stop at the same double-precision residual, so their
+    steps agree within the mixed-precision bound; the mixed form reports the
+    residual of its double-precision iterate."""
+    w = inputs.workload("spinodal64")
+    outs = []
+    for precision in PRECISIONS:
+        with _run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], precision) as run:
+            run.set_phi(w["phi0"])
+            s, v, r = run.step(20)
+            assert r <= 1e-10
+            outs.append(run.get_phi())
+    assert np.max(np.abs(outs[0] - outs[1])) <= PHI_TOL[1]
 
 
 def test_not_converged_keeps_state():
