@@ -122,6 +122,15 @@ __device__ __forceinline__ T inv_count(int n) {
          : n == 5 ? T(0.2) : T(1);
 }
 
+// Programmatic dependent launch: the kernels of a step are launched so that
+// each may be scheduled while its predecessor drains (its blocks trigger the
+// launch implicitly when they exit), and each first waits until the
+// predecessor grid has completed and its writes are visible.  No block
+// triggers early, so a successor's blocks are never placed on the SMs before
+// its predecessor has finished issuing work (an early trigger unbalanced the
+// large grids).
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void cell_ijk(int c, int nx, int ny, int& i, int& j, int& k) {
   i = c % nx;
   int r = c / nx;
@@ -184,6 +193,7 @@ __device__ __forceinline__ void eval_N(const Level<T>& L, const Coefs<T>& K, con
 //   Ae = (s/h^2)(sM - gamma sa^2 / n_c),  C/Dn = s sa / n_c,  G = gamma sa / h^2.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_coef(Level<T> L, Coefs<T> K) {
+  pdl_enter();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.ncell) return;
   int i, j, k;
@@ -280,6 +290,7 @@ __device__ __forceinline__ void cell_rhs(const Level<T>& L, const Coefs<T>& K, i
 // row's first cell of the colour at i = (j + k + colour) & 1.
 template <typename T, int DIM, bool CORR>
 __global__ void __launch_bounds__(kSmoothBlock) k_smooth(Level<T> L, Coefs<T> K, int colour, int rhs) {
+  pdl_enter();
   const int hw = (L.nx + 1) >> 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int row = t / hw;
@@ -298,6 +309,7 @@ __global__ void __launch_bounds__(kSmoothBlock) k_smooth(Level<T> L, Coefs<T> K,
 // carry it).
 template <typename T, int DIM, bool CORR>
 __global__ void __launch_bounds__(kBlock) k_coarse_rhs(Level<T> C, Coefs<T> K) {
+  pdl_enter();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= C.ncell) return;
   int i, j, k;
@@ -315,6 +327,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rhs(Level<T> C, Coefs<T> K) {
 // R phi_b in correction form, and f_c = R r (completed later by N_c(R u)).
 template <typename T, int DIM, bool CORR>
 __global__ void __launch_bounds__(kBlock) k_residual_restrict(Level<T> F, Level<T> C, Coefs<T> K) {
+  pdl_enter();
   constexpr int TX = DIM == 3 ? 8 : 16;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -367,6 +380,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(Level<T> F, Level<
 // u += P(u_c - u_c^0), P piecewise constant.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
+  pdl_enter();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= F.ncell) return;
   int i, j, k;
@@ -380,6 +394,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
 // phi^m and phi* on the coarse grid: mean of the children (once per step).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_restrict_coef(Level<T> F, Level<T> C) {
+  pdl_enter();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= C.ncell) return;
   int I, J, KK;
@@ -469,6 +484,7 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, in
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double* partials, DevState* st,
                                                  cudaGraphConditionalHandle cond, int mode, int use_cond) {
+  pdl_enter();
   __shared__ bool last;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
@@ -511,6 +527,7 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
 // phi^m and phi* of the finest grid in single precision (once per step).
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_to_f32(Level<double> F, Level<float> G) {
+  pdl_enter();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= F.ncell) return;
   G.phim[c] = (float)F.phim[c];
@@ -524,6 +541,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<double> K, Level<float> G,
                                                        double* partials, DevState* st,
                                                        cudaGraphConditionalHandle cond, int mode, int use_cond) {
+  pdl_enter();
   __shared__ bool last;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
@@ -562,6 +580,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
 
 // u <- u + e in double precision.
 static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L, Level<float> G) {
+  pdl_enter();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.ncell) return;
   L.phi[c] += (double)G.phi[c];
@@ -577,6 +596,7 @@ static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L,
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_setup(Level<double> L, const double* phimm1, double eps2,
                                                   const DevState* st) {
+  pdl_enter();
   if (st->failed) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.ncell) return;
@@ -603,6 +623,7 @@ __global__ void __launch_bounds__(kBlock) k_setup(Level<double> L, const double*
 
 // Partial sums of v (NV = 1), one per block.
 static __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* v, int n, double* partials) {
+  pdl_enter();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {c < n ? v[c] : 0.0};
   block_sum<1>(acc);
@@ -610,6 +631,7 @@ static __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* v, 
 }
 
 static __global__ void k_mean_finish(const double* partials, int nparts, int n, DevState* st) {
+  pdl_enter();
   double tot[1];
   sum_partials<1>(partials, nparts, tot);
   if (threadIdx.x == 0) st->pmean = tot[0] / n;
@@ -617,6 +639,7 @@ static __global__ void k_mean_finish(const double* partials, int nparts, int n, 
 
 // Accept the step: phi^{m-1} <- phi^m, phi^m <- phi^{m+1}, p <- p - mean(p).
 static __global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, double* phimm1, DevState* st) {
+  pdl_enter();
   if (st->failed) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c == 0) {
@@ -751,11 +774,73 @@ __device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>
   }
 }
 
+// Fields of a tail level held in shared memory, in carving order.  The
+// per-step coefficients (phi^m, a, M, their sums, Ae, C/Dn, G) are copied in
+// on every level, the state and right-hand sides (phi, mu, p, f, R u, phi_b)
+// only on the tail's top level; the levels below are computed in place.
+template <int DIM, bool CORR>
+__host__ __device__ constexpr int tail_fields() { return 19 + (DIM == 3 ? 2 : 0) + (CORR ? 1 : 0); }
+
+__host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename T, int DIM, bool CORR>
+__host__ __device__ inline size_t tail_smem_bytes(const int* ncell, int n) {
+  size_t b = 0;
+  for (int l = 0; l < n; ++l) b += tail_fields<DIM, CORR>() * tail_align(sizeof(T) * ncell[l]);
+  return b;
+}
+
 template <typename T, int DIM, bool CORR>
 __global__ void __launch_bounds__(kTailThreads) k_tail(Tail<T> tl, Coefs<T> K) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  __shared__ Level<T> sl[kTailMaxLevels];
   const int n = tl.n;
+  if (threadIdx.x == 0) {
+    size_t off = 0;
+    auto carve = [&](int nc) {
+      T* p = reinterpret_cast<T*>(tail_smem + off);
+      off += tail_align(sizeof(T) * nc);
+      return p;
+    };
+    for (int l = 0; l < n; ++l) {
+      Level<T> L = tl.lev[l];
+      const int nc = L.ncell;
+      L.phi = carve(nc); L.mu = carve(nc); L.p = carve(nc);
+      L.fphi = carve(nc); L.fmu = carve(nc); L.fp = carve(nc);
+      L.phim = carve(nc); L.phi0 = carve(nc); L.mu0 = carve(nc); L.p0 = carve(nc);
+      L.ax = carve(nc); L.ay = carve(nc); L.Mx = carve(nc); L.My = carve(nc);
+      L.sM = carve(nc); L.sa = carve(nc); L.cAe = carve(nc); L.cCD = carve(nc); L.cG = carve(nc);
+      if (DIM == 3) { L.az = carve(nc); L.Mz = carve(nc); }
+      if (CORR) L.phib = carve(nc);
+      L.phis = nullptr;
+      sl[l] = L;
+    }
+  }
+  __syncthreads();
+  auto copy = [&](T* dst, const T* src, int nc) {
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) dst[c] = src[c];
+  };
+  for (int l = 0; l < n; ++l) {
+    const Level<T>& G = tl.lev[l];
+    const Level<T>& S = sl[l];
+    const int nc = G.ncell;
+    copy(S.phim, G.phim, nc);
+    copy(S.ax, G.ax, nc); copy(S.ay, G.ay, nc); copy(S.Mx, G.Mx, nc); copy(S.My, G.My, nc);
+    copy(S.sM, G.sM, nc); copy(S.sa, G.sa, nc);
+    copy(S.cAe, G.cAe, nc); copy(S.cCD, G.cCD, nc); copy(S.cG, G.cG, nc);
+    if (DIM == 3) { copy(S.az, G.az, nc); copy(S.Mz, G.Mz, nc); }
+    if (l == 0) {
+      copy(S.phi, G.phi, nc); copy(S.mu, G.mu, nc); copy(S.p, G.p, nc);
+      copy(S.fphi, G.fphi, nc); copy(S.fmu, G.fmu, nc); copy(S.fp, G.fp, nc);
+      copy(S.phi0, G.phi0, nc); copy(S.mu0, G.mu0, nc); copy(S.p0, G.p0, nc);
+      if (CORR) copy(S.phib, G.phib, nc);
+    }
+  }
+  __syncthreads();
+
   for (int l = 0; l + 1 < n; ++l) {
-    const Level<T>& L = tl.lev[l];
+    const Level<T>& L = sl[l];
     bool rhs = l > 0 || tl.top_rhs;
     if (rhs && tl.nu1 == 0) {
       tail_rhs<T, DIM, CORR>(L, K);
@@ -763,15 +848,21 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(Tail<T> tl, Coefs<T> K) {
     }
     for (int it = 0; it < tl.nu1; ++it)
       for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(L, K, colour, rhs && it == 0);
-    tail_restrict<T, DIM, CORR>(L, tl.lev[l + 1], K);
+    tail_restrict<T, DIM, CORR>(L, sl[l + 1], K);
   }
-  if (n > 1 || tl.top_rhs) tail_rhs<T, DIM, CORR>(tl.lev[n - 1], K);
-  coarsest_solve<T, DIM, CORR>(tl.lev[n - 1], K);
+  if (n > 1 || tl.top_rhs) tail_rhs<T, DIM, CORR>(sl[n - 1], K);
+  coarsest_solve<T, DIM, CORR>(sl[n - 1], K);
   for (int l = n - 2; l >= 0; --l) {
-    tail_prolong<T, DIM>(tl.lev[l], tl.lev[l + 1]);
+    tail_prolong<T, DIM>(sl[l], sl[l + 1]);
     for (int it = 0; it < tl.nu2; ++it)
-      for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(tl.lev[l], K, colour, false);
+      for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(sl[l], K, colour, false);
   }
+
+  const Level<T>& G = tl.lev[0];
+  const Level<T>& S = sl[0];
+  copy(G.phi, S.phi, G.ncell);
+  copy(G.mu, S.mu, G.ncell);
+  copy(G.p, S.p, G.ncell);
 }
 
 // ---------------------------------------------------------------- diagnostics
