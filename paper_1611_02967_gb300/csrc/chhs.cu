@@ -18,10 +18,12 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/chhs.h"
 #include "chhs_kernels.cuh"
+#include "chhs_tile.cuh"
 
 using namespace chhs_dev;
 
@@ -222,6 +224,21 @@ void pdl_smem(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaSt
 }
 
 template <typename... KArgs, typename... Args>
+void pdl_grid(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... KArgs, typename... Args>
 void pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
   pdl_smem(kernel, grid, block, 0, s, args...);
 }
@@ -272,6 +289,23 @@ struct Enqueue {
     }
     const Level<T>& C = lev[l + 1];
     const bool rhs = l > 0;
+    if constexpr (use_tiles<T>()) {
+      // 2D single precision: pre-smoothing (+ right-hand side) + residual +
+      // restriction in one tiled launch, prolongation + post-smoothing in another
+      const dim3 grid((L.nx + kTileW - 1) / kTileW, (L.ny + kTileH - 1) / kTileH);
+      const int nf = tile_nfields<CORR>();
+      const int np1 = 2 * run->opts.nu1, np2 = 2 * run->opts.nu2;
+      launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu1, [&] {
+        pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
+                 np1 + 1, rhs ? 1 : 0, 0, 1);
+      });
+      vcycle<T, CORR>(run, s, lev, tail, l + 1);
+      launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu2, [&] {
+        pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np2, nf, sizeof(T)), s, L, C, K, np2, np2,
+                 0, 1, 0);
+      });
+      return;
+    }
     if (rhs && run->opts.nu1 == 0)
       launch(run, s, CHHS_K_COARSE_RHS, L.ncell, [&] {
         pdl(k_coarse_rhs<T, DIM, CORR>, nblocks(L.ncell), kBlock, s, L, K);
@@ -292,6 +326,10 @@ struct Enqueue {
 
   static bool mixed(const chhs_t* run) { return run->opts.precision == 1; }
 
+  // The fused tile kernels serve the 2D single-precision V-cycles.
+  template <typename T>
+  static constexpr bool use_tiles() { return DIM == 2 && std::is_same<T, float>::value; }
+
   template <typename T, bool CORR>
   static size_t tail_bytes(const Tail<T>& tail) {
     int nc[kTailMaxLevels];
@@ -304,6 +342,11 @@ struct Enqueue {
   static chhs_status prepare_tail(chhs_t* run, const Tail<T>& tail) {
     const size_t smem = tail_bytes<T, CORR>(tail);
     CU(cudaFuncSetAttribute(k_tail<T, DIM, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (use_tiles<T>()) {
+      const int halo = 2 * std::max(run->opts.nu1, run->opts.nu2) + 1;
+      const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T));
+      CU(cudaFuncSetAttribute(k_tile<T, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb));
+    }
     return CHHS_OK;
   }
 
