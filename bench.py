@@ -323,19 +323,19 @@ def run_ours(args):
         prof = run.profile_step(prof)
     total_ms = sum(v[0] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][0])
-    sm_ms, sm_launch, sm_units = prof["smooth"]
-    flops = sm_units * SMOOTH_FLOPS[2]
-    achieved = flops / (sm_ms / 1e3) / 1e12
+    sm_ms, sm_launch, sm_units = prof["smooth_finest"]
+    flops_per_launch = sm_units / sm_launch * SMOOTH_FLOPS[2]
+    avg_s = sm_ms / sm_launch / 1e3
+    achieved = flops_per_launch / avg_s / 1e12
     traffic = measured_traffic()
-    roofline = {"bound": "alu", "kernel": "k_smooth<double,2> (FP64 red-black cell update)",
+    roofline = {"bound": "alu", "kernel": "k_smooth<double,2,false> on the 512x512 level (FP64 red-black cell update)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal FP64 152 SMs x 2.07 GHz x 4 flop/clk (recipe's unit counts)",
-                "traffic": traffic, "dominant_kernel_share": prof["smooth"][0] / total_ms,
-                "avg_launch_us": 1e3 * sm_ms / sm_launch,
-                "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in prof.items()}}
-    if dom != "smooth":
-        roofline["note"] = "largest device-time share this run: %s" % dom
+                "traffic": traffic, "flop_per_launch": flops_per_launch,
+                "avg_launch_us": 1e6 * avg_s, "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in prof.items()},
+                "kernel_us_per_launch": {k: round(1e3 * v[0] / v[1], 2) for k, v in prof.items() if v[1]},
+                "largest_share": dom}
 
     # the mixed-precision form on the same workload and steps, timed the same way
     run32 = chhs.Run(shape, w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream,
@@ -350,7 +350,15 @@ def run_ours(args):
     run.set_state(*state0)
     run.step(args.steps)
     diff = float(np.max(np.abs(run.get_phi() - run32.get_phi())))
+    mprof = None
+    run32.set_state(*state0)
+    for _ in range(5):
+        mprof = run32.profile_step(mprof)
+    mtot = sum(v[0] for v in mprof.values())
     mixed = {"value": units / (mx_max / 1e3), "unit": UNIT, "ms_per_step": mx_max / args.steps,
+             "kernel_shares": {k: round(v[0] / mtot, 4) for k, v in mprof.items()},
+             "kernel_us_per_launch": {k: round(1e3 * v[0] / v[1], 2) for k, v in mprof.items() if v[1]},
+             "smooth_finest_avg_launch_us": 1e3 * mprof["smooth_finest"][0] / max(1, mprof["smooth_finest"][1]),
              "vcycles_per_step": mx_v / args.steps, "final_resid": mx_resid,
              "dtype": "f32 V-cycles, f64 residual/update/norms",
              "max_abs_phi_diff_vs_f64_after_K_steps": diff}

@@ -61,9 +61,9 @@ constexpr int kBaseFields = 11;
 int level_fields(int dim, bool single) { return kBaseFields + (dim == 3 ? 11 : 9) + (single ? 1 : 0); }
 
 // Levels with at most this many cells run inside the one-block tail kernel.
-// In double precision one SM does 2 FMA per clock, so only the tiniest levels
-// (8 x 8, 4 x 4 x 4) are cheaper there than as grid-wide launches; in single
-// precision (64x the rate) levels up to 32 x 32 are.
+// In double precision one SM does 2 FMA per clock and a single warp's
+// dependent FP64 chain is slow, so only the tiniest levels (8 x 8, 4 x 4 x 4)
+// go there; in single precision (64x the rate) levels up to 32 x 32 do.
 constexpr int kTailCellsF64 = 64;
 constexpr int kTailCellsF32 = 1024;
 
@@ -379,40 +379,35 @@ struct Enqueue {
 
   static void frame_head(chhs_t* run, cudaStream_t s) {
     const Level<double>& F = run->lev[0];
-    launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-      pdl(k_setup<DIM>, nblocks(F.ncell), kBlock, s, F, run->phimm1, run->eps * run->eps, run->st);
-    });
-    for (size_t l = 1; l < run->lev.size(); ++l)
-      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-        pdl(k_restrict_coef<double, DIM>, nblocks(run->lev[l].ncell), kBlock, s, run->lev[l - 1], run->lev[l]);
-      });
     const Coefs<double> K = coefs<double>(run);
-    for (size_t l = 0; l < run->lev.size(); ++l)
+    const std::vector<Level<double>>& D = run->lev;
+    const int nd = (int)D.size();
+    launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+      pdl(k_setup_coef<DIM>, nblocks(F.ncell), kBlock, s, F, run->phimm1, run->eps * run->eps, run->st, K,
+          nd > 1 ? D[1] : D[0], nd > 1 ? 1 : 0);
+    });
+    for (int l = 1; l < nd; ++l)
       launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-        pdl(k_coef<double, DIM>, nblocks(run->lev[l].ncell), kBlock, s, run->lev[l], K);
+        pdl(k_coef_restrict<double, DIM>, nblocks(D[l].ncell), kBlock, s, D[l], K, l + 1 < nd ? D[l + 1] : D[l],
+            l + 1 < nd ? 1 : 0);
       });
     if (!mixed(run)) return;
     const std::vector<Level<float>>& G = run->lev32;
-    launch(run, s, CHHS_K_FRAME, 1.0, [&] { pdl(k_to_f32<DIM>, nblocks(F.ncell), kBlock, s, F, G[0]); });
-    for (size_t l = 1; l < G.size(); ++l)
-      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-        pdl(k_restrict_coef<float, DIM>, nblocks(G[l].ncell), kBlock, s, G[l - 1], G[l]);
-      });
+    const int ng = (int)G.size();
     const Coefs<float> K32 = coefs<float>(run);
-    for (size_t l = 0; l < G.size(); ++l)
+    launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+      pdl(k_coef_restrict_f32<DIM>, nblocks(F.ncell), kBlock, s, F, G[0], K32, ng > 1 ? G[1] : G[0],
+          ng > 1 ? 1 : 0);
+    });
+    for (int l = 1; l < ng; ++l)
       launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-        pdl(k_coef<float, DIM>, nblocks(G[l].ncell), kBlock, s, G[l], K32);
+        pdl(k_coef_restrict<float, DIM>, nblocks(G[l].ncell), kBlock, s, G[l], K32, l + 1 < ng ? G[l + 1] : G[l],
+            l + 1 < ng ? 1 : 0);
       });
   }
 
   static void frame_tail(chhs_t* run, cudaStream_t s) {
     const Level<double>& F = run->lev[0];
-    launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-      pdl(k_sum_partial, nblocks(F.ncell), kBlock, s, F.p, F.ncell, run->partials);
-    });
-    launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-      pdl(k_mean_finish, 1, 1024, s, run->partials, nblocks(F.ncell), F.ncell, run->st);
-    });
     launch(run, s, CHHS_K_FRAME, 1.0, [&] {
       pdl(k_advance, nblocks(F.ncell), kBlock, s, F, run->phimm1, run->st);
     });

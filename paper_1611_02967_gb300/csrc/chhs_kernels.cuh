@@ -187,22 +187,20 @@ __device__ __forceinline__ void eval_N(const Level<T>& L, const Coefs<T>& K, con
   n3 = -L.ih2 * ((S.p - mm * pc) + K.gamma * (S.amu - sa * muc));
 }
 
-// Coefficients of a time step on one level, from phi*: the face values
-// a_f = (phi*_c + phi*_e)/2 and M_f = 1 + gamma a_f^2 on the +x/+y/+z faces,
-// sM = sum M_f and sa = sum a_f over the interior faces, and the smoother's
+// Coefficients of a time step at cell c of one level, from phi*: the face
+// values a_f = (phi*_c + phi*_e)/2 and M_f = 1 + gamma a_f^2 on the
+// +x/+y/+z faces, sM = sum M_f and sa = sum a_f over the interior faces, and
+// the smoother's
 //   Ae = (s/h^2)(sM - gamma sa^2 / n_c),  C/Dn = s sa / n_c,  G = gamma sa / h^2.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_coef(Level<T> L, Coefs<T> K) {
-  pdl_enter();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.ncell) return;
-  int i, j, k;
-  cell_ijk(c, L.nx, L.ny, i, j, k);
-  const T ps = L.phis[c];
+// ps(e) returns phi* at cell e.
+template <typename T, int DIM, class PS>
+__device__ __forceinline__ void coef_at(const Level<T>& L, const Coefs<T>& K, int c, int i, int j, int k,
+                                        PS ps) {
+  const T pc = ps(c);
   T sumM = 0, suma = 0;
   int m = 0;
   auto face = [&](int e, T* a_out, T* M_out) {
-    T a = T(0.5) * (ps + L.phis[e]);
+    T a = T(0.5) * (pc + ps(e));
     T M = T(1) + K.gamma * a * a;
     sumM += M;
     suma += a;
@@ -230,6 +228,42 @@ __global__ void __launch_bounds__(kBlock) k_coef(Level<T> L, Coefs<T> K) {
   L.cAe[c] = L.sih2 * (sumM - K.gamma * suma * suma * im);
   L.cCD[c] = K.s * suma * im;
   L.cG[c] = K.gamma * L.ih2 * suma;
+}
+
+// phi^m and phi* of the 2^d-cell block whose corner is (i, j, k), restricted
+// (mean of the children) into the next coarser level; pm(e), ps(e) give the
+// fine values.
+template <typename T, typename U, int DIM, class PM, class PS>
+__device__ __forceinline__ void restrict_coef_at(const Level<U>& F, const Level<T>& C, int i, int j, int k,
+                                                 PM pm, PS ps) {
+  T a = 0, b = 0;
+  const int kz = DIM == 3 ? 2 : 1;
+  for (int dk = 0; dk < kz; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        int e = (i + di) + F.nx * ((j + dj) + F.ny * (k + dk));
+        a += pm(e);
+        b += ps(e);
+      }
+  const T w = DIM == 3 ? T(0.125) : T(0.25);
+  int q = (i >> 1) + C.nx * ((j >> 1) + C.ny * (k >> 1));
+  C.phim[q] = w * a;
+  C.phis[q] = w * b;
+}
+
+// A level's coefficients, and the restriction of phi^m and phi* to the next
+// level (has_next), in one pass.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_coef_restrict(Level<T> L, Coefs<T> K, Level<T> Cn, int has_next) {
+  pdl_enter();
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.ncell) return;
+  int i, j, k;
+  cell_ijk(c, L.nx, L.ny, i, j, k);
+  auto ps = [&](int e) { return L.phis[e]; };
+  auto pm = [&](int e) { return L.phim[e]; };
+  coef_at<T, DIM>(L, K, c, i, j, k, ps);
+  if (has_next && !(i & 1) && !(j & 1) && (DIM == 2 || !(k & 1))) restrict_coef_at<T, T, DIM>(L, Cn, i, j, k, pm, ps);
 }
 
 // ---------------------------------------------------------------- smoother
@@ -391,28 +425,6 @@ __global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
   F.p[c] += C.p[q] - C.p0[q];
 }
 
-// phi^m and phi* on the coarse grid: mean of the children (once per step).
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_restrict_coef(Level<T> F, Level<T> C) {
-  pdl_enter();
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= C.ncell) return;
-  int I, J, KK;
-  cell_ijk(q, C.nx, C.ny, I, J, KK);
-  T a = 0, b = 0;
-  const int kz = DIM == 3 ? 2 : 1;
-  for (int dk = 0; dk < kz; ++dk)
-    for (int dj = 0; dj < 2; ++dj)
-      for (int di = 0; di < 2; ++di) {
-        int c = (2 * I + di) + F.nx * ((2 * J + dj) + F.ny * (2 * KK + dk));
-        a += F.phim[c];
-        b += F.phis[c];
-      }
-  const T w = DIM == 3 ? T(0.125) : T(0.25);
-  C.phim[q] = w * a;
-  C.phis[q] = w * b;
-}
-
 // ---------------------------------------------------------------- reductions
 
 template <typename T>
@@ -478,16 +490,17 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, in
 }
 
 // Stopping norm sqrt(mean over cells of r_phi^2 + r_mu^2 + (s r_p)^2) on the
-// finest grid, in one launch: every block writes its partial sum, and the
+// finest grid, in one launch: every block writes its partial sums, and the
 // last block to finish (ticket counter) adds the partials in a fixed order and
 // takes the loop decision, setting the while-loop condition of the step graph.
+// It also records the mean of p (removed when the step is accepted).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double* partials, DevState* st,
                                                  cudaGraphConditionalHandle cond, int mode, int use_cond) {
   pdl_enter();
   __shared__ bool last;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   if (c < L.ncell) {
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
@@ -496,20 +509,23 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
     double r1 = double(L.fphi[c] - n1), r2 = double(L.fmu[c] - n2);
     double r3 = double(K.s) * double(L.fp[c] - n3);
     acc[0] = r1 * r1 + r2 * r2 + r3 * r3;
+    acc[1] = double(L.p[c]);
   }
-  block_sum<1>(acc);
+  block_sum<2>(acc);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x + 1] = acc[1];
     __threadfence();
     last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot[1];
-  sum_partials<1>(partials, gridDim.x, tot);
+  double tot[2];
+  sum_partials<2>(partials, gridDim.x, tot);
   if (threadIdx.x != 0) return;
   st->ticket = 0;
+  st->pmean = tot[1] / L.ncell;
   unsigned int go = loop_decision(st, sqrt(tot[0] / L.ncell), mode);
   if (use_cond) cudaGraphSetConditional(cond, go);
 }
@@ -524,14 +540,23 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
 // solve is relative to the correction, not to u, so the outer loop reaches
 // the double-precision tolerance.
 
-// phi^m and phi* of the finest grid in single precision (once per step).
+// The single-precision finest level of a step: phi^m and phi* rounded, its
+// coefficients, and the restriction to the next single-precision level.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_to_f32(Level<double> F, Level<float> G) {
+__global__ void __launch_bounds__(kBlock) k_coef_restrict_f32(Level<double> F, Level<float> G, Coefs<float> K,
+                                                              Level<float> Gn, int has_next) {
   pdl_enter();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= F.ncell) return;
-  G.phim[c] = (float)F.phim[c];
-  G.phis[c] = (float)F.phis[c];
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  auto ps = [&](int e) { return (float)F.phis[e]; };
+  auto pm = [&](int e) { return (float)F.phim[e]; };
+  G.phim[c] = pm(c);
+  G.phis[c] = ps(c);
+  coef_at<float, DIM>(G, K, c, i, j, k, ps);
+  if (has_next && !(i & 1) && !(j & 1) && (DIM == 2 || !(k & 1)))
+    restrict_coef_at<float, double, DIM>(F, Gn, i, j, k, pm, ps);
 }
 
 // The stopping norm of the double-precision iterate, as k_norm, and the
@@ -544,7 +569,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
   pdl_enter();
   __shared__ bool last;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   if (c < L.ncell) {
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
@@ -553,6 +578,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
     double r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = L.fp[c] - n3;
     double r3s = K.s * r3;
     acc[0] = r1 * r1 + r2 * r2 + r3s * r3s;
+    acc[1] = L.p[c];
     G.fphi[c] = (float)r1;
     G.fmu[c] = (float)r2;
     G.fp[c] = (float)r3;
@@ -561,19 +587,21 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
     G.p[c] = 0.f;
     G.phib[c] = (float)L.phi[c];
   }
-  block_sum<1>(acc);
+  block_sum<2>(acc);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x + 1] = acc[1];
     __threadfence();
     last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot[1];
-  sum_partials<1>(partials, gridDim.x, tot);
+  double tot[2];
+  sum_partials<2>(partials, gridDim.x, tot);
   if (threadIdx.x != 0) return;
   st->ticket = 0;
+  st->pmean = tot[1] / L.ncell;
   unsigned int go = loop_decision(st, sqrt(tot[0] / L.ncell), mode);
   if (use_cond) cudaGraphSetConditional(cond, go);
 }
@@ -593,9 +621,12 @@ static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L,
 // phi* = 3/2 phi^m - 1/2 phi^{m-1} (Eq. 2.4); f_phi = phi^m;
 // f_mu = -phi* - (1/4) eps^2 Lap_h phi^{m-1}; f_p = 0; initial guess
 // phi = 2 phi^m - phi^{m-1} (mu and p keep the previous step's values).
+// Fused: the finest level's coefficients (phi* of the neighbours formed on
+// the fly) and the restriction of phi^m, phi* to the next level (has_next).
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_setup(Level<double> L, const double* phimm1, double eps2,
-                                                  const DevState* st) {
+__global__ void __launch_bounds__(kBlock) k_setup_coef(Level<double> L, const double* phimm1, double eps2,
+                                                       const DevState* st, Coefs<double> K, Level<double> Cn,
+                                                       int has_next) {
   pdl_enter();
   if (st->failed) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -619,22 +650,11 @@ __global__ void __launch_bounds__(kBlock) k_setup(Level<double> L, const double*
   L.fmu[c] = -ps - 0.25 * eps2 * L.ih2 * lap;
   L.fp[c] = 0.0;
   L.phi[c] = 2.0 * pm - pmm;
-}
-
-// Partial sums of v (NV = 1), one per block.
-static __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* v, int n, double* partials) {
-  pdl_enter();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {c < n ? v[c] : 0.0};
-  block_sum<1>(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
-}
-
-static __global__ void k_mean_finish(const double* partials, int nparts, int n, DevState* st) {
-  pdl_enter();
-  double tot[1];
-  sum_partials<1>(partials, nparts, tot);
-  if (threadIdx.x == 0) st->pmean = tot[0] / n;
+  auto psf = [&](int e) { return 1.5 * L.phim[e] - 0.5 * phimm1[e]; };
+  auto pmf = [&](int e) { return L.phim[e]; };
+  coef_at<double, DIM>(L, K, c, i, j, k, psf);
+  if (has_next && !(i & 1) && !(j & 1) && (DIM == 2 || !(k & 1)))
+    restrict_coef_at<double, double, DIM>(L, Cn, i, j, k, pmf, psf);
 }
 
 // Accept the step: phi^{m-1} <- phi^m, phi^m <- phi^{m+1}, p <- p - mean(p).
@@ -818,26 +838,34 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(Tail<T> tl, Coefs<T> K) {
     }
   }
   __syncthreads();
-  auto copy = [&](T* dst, const T* src, int nc) {
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) dst[c] = src[c];
-  };
+  // Copy in: per cell, every field is loaded before any is stored, so a
+  // thread's loads are all in flight together.
   for (int l = 0; l < n; ++l) {
     const Level<T>& G = tl.lev[l];
     const Level<T>& S = sl[l];
-    const int nc = G.ncell;
-    copy(S.phim, G.phim, nc);
-    copy(S.ax, G.ax, nc); copy(S.ay, G.ay, nc); copy(S.Mx, G.Mx, nc); copy(S.My, G.My, nc);
-    copy(S.sM, G.sM, nc); copy(S.sa, G.sa, nc);
-    copy(S.cAe, G.cAe, nc); copy(S.cCD, G.cCD, nc); copy(S.cG, G.cG, nc);
-    if (DIM == 3) { copy(S.az, G.az, nc); copy(S.Mz, G.Mz, nc); }
-    if (l == 0) {
-      copy(S.phi, G.phi, nc); copy(S.mu, G.mu, nc); copy(S.p, G.p, nc);
-      copy(S.fphi, G.fphi, nc); copy(S.fmu, G.fmu, nc); copy(S.fp, G.fp, nc);
-      copy(S.phi0, G.phi0, nc); copy(S.mu0, G.mu0, nc); copy(S.p0, G.p0, nc);
-      if (CORR) copy(S.phib, G.phib, nc);
+    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
+      T v[12];
+      v[0] = G.phim[c]; v[1] = G.ax[c]; v[2] = G.ay[c]; v[3] = G.Mx[c]; v[4] = G.My[c];
+      v[5] = G.sM[c]; v[6] = G.sa[c]; v[7] = G.cAe[c]; v[8] = G.cCD[c]; v[9] = G.cG[c];
+      if (DIM == 3) { v[10] = G.az[c]; v[11] = G.Mz[c]; }
+      S.phim[c] = v[0]; S.ax[c] = v[1]; S.ay[c] = v[2]; S.Mx[c] = v[3]; S.My[c] = v[4];
+      S.sM[c] = v[5]; S.sa[c] = v[6]; S.cAe[c] = v[7]; S.cCD[c] = v[8]; S.cG[c] = v[9];
+      if (DIM == 3) { S.az[c] = v[10]; S.Mz[c] = v[11]; }
+      if (l == 0) {
+        T u[10];
+        u[0] = G.phi[c]; u[1] = G.mu[c]; u[2] = G.p[c]; u[3] = G.fphi[c]; u[4] = G.fmu[c]; u[5] = G.fp[c];
+        u[6] = G.phi0[c]; u[7] = G.mu0[c]; u[8] = G.p0[c];
+        if (CORR) u[9] = G.phib[c];
+        S.phi[c] = u[0]; S.mu[c] = u[1]; S.p[c] = u[2]; S.fphi[c] = u[3]; S.fmu[c] = u[4]; S.fp[c] = u[5];
+        S.phi0[c] = u[6]; S.mu0[c] = u[7]; S.p0[c] = u[8];
+        if (CORR) S.phib[c] = u[9];
+      }
     }
   }
   __syncthreads();
+  auto copy = [&](T* dst, const T* src, int nc) {
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) dst[c] = src[c];
+  };
 
   for (int l = 0; l + 1 < n; ++l) {
     const Level<T>& L = sl[l];
