@@ -112,14 +112,17 @@ chhs_status chhs_launch_counts(const chhs_t* run, int* per_vcycle, int* per_step
 
 /* Kernel kinds reported by chhs_profile_step. */
 enum {
-    CHHS_K_SMOOTH = 0,      /* one colour pass of the nonlinear Gauss-Seidel smoother; units: cells updated */
+    CHHS_K_SMOOTH = 0,      /* one colour pass of the nonlinear Gauss-Seidel smoother on a coarse
+                               level; units: cells updated */
     CHHS_K_RESTRICT = 1,    /* residual + restriction to the next level; units: fine cells */
     CHHS_K_COARSE_RHS = 2,  /* FAS coarse right-hand side; units: coarse cells */
     CHHS_K_PROLONG = 3,     /* prolongation + correction; units: fine cells */
     CHHS_K_COARSEST = 4,    /* coarsest-grid solve; units: 1 per launch */
     CHHS_K_NORM = 5,        /* stopping norm on the finest grid; units: cells */
-    CHHS_K_FRAME = 6,       /* setup, coefficient restriction, mean of p, accept; units: launches */
-    CHHS_K_COUNT = 7
+    CHHS_K_FRAME = 6,       /* setup, coefficient restriction, mean of p, accept, and the
+                               mixed form's double-precision update; units: launches */
+    CHHS_K_SMOOTH_FINEST = 7, /* the smoother on the finest level; units: cells updated */
+    CHHS_K_COUNT = 8
 };
 
 /* Advance one time step exactly as chhs_step(run, 1) does, but launch the
@@ -134,6 +137,15 @@ chhs_status chhs_mass(chhs_t* run, double* mass_out);
 
 /* E_h(phi^m) (Eq. 2.8) and, if F_out is not NULL, F_h(phi^m, phi^{m-1}) (Eq. 2.9). */
 chhs_status chhs_energy(chhs_t* run, double* E_out, double* F_out);
+
+/* Dissipation terms of the last accepted step (Eq. 2.23 and the proof of
+ * Theorem 2.1): grad_mu_sq = ||grad_h mu^{m-1/2}||_2^2 and
+ * u_sq = ||u^{m-1/2}||_2^2 with the velocity of Eq. 2.3,
+ * u = -grad_h p - gamma A_h phi* grad_h mu, on the face grid (zero normal
+ * velocity on boundary faces), and div_u_max = max over cells of
+ * |div_h u| (Eq. 2.7 makes it zero up to the solver's residual).  Each output
+ * is nullable.  Meaningful after at least one chhs_step. */
+chhs_status chhs_dissipation(chhs_t* run, double* grad_mu_sq, double* u_sq, double* div_u_max);
 
 /* Copy out phi^m (the latest accepted step). */
 chhs_status chhs_get_phi(chhs_t* run, double* out, int on_device);
@@ -175,6 +187,54 @@ chhs_status chhs_set_state(chhs_t* run, const double* phi, const double* phi_pre
 chhs_status chhs_energy_noalloc(int dim, const int n[3], double h, double eps, const double* phi_dev,
                                 const double* psi_dev, void* cuda_stream, double* mass_out,
                                 double* E_out, double* F_out);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop for many independent runs on one GPU (continuous batching).
+ * A worker thread admits submitted runs first come, first served, whenever an
+ * active slot is free and the run's hierarchy (chhs_workspace_bytes) fits in
+ * a device memory pool allocated once at creation; each active run has its
+ * own stream and advances steps_per_slice steps at a time, so runs overlap on
+ * the device, and between slices finished runs are retired (their memory
+ * returns to the pool) and waiting runs admitted.  Each run computes exactly
+ * what chhs_create + chhs_set_phi + chhs_step would compute for it alone. */
+typedef struct chhs_server chhs_server_t;
+
+typedef struct {
+    int dim;               /* 2 or 3 */
+    int n[3];              /* grid size (n[2] ignored in 2D) */
+    double h, eps, gamma, dt;
+    int nsteps;            /* time steps to take */
+    int precision;         /* as chhs_opts.precision; other options are the defaults */
+    const double* phi0;    /* host, copied at submit: phi^0 */
+    const double* phi_prev;/* host, copied at submit, or NULL: phi^{-1} = phi^0 */
+} chhs_request;
+
+/* Start a server with a device pool of pool_bytes, at most max_active runs
+ * on the GPU at once and steps_per_slice steps per launch slice. */
+chhs_status chhs_server_create(size_t pool_bytes, int max_active, int steps_per_slice, chhs_server_t** out);
+
+/* Queue a run; *id_out identifies it.  INVALID_ARG for a bad request.  A run
+ * whose hierarchy exceeds the whole pool finishes with CHHS_ERR_OOM. */
+chhs_status chhs_server_submit(chhs_server_t* sv, const chhs_request* req, long long* id_out);
+
+/* Block until run id is done or timeout_s seconds pass (then
+ * CHHS_ERR_NOT_CONVERGED is returned and the run keeps going). */
+chhs_status chhs_server_wait(chhs_server_t* sv, long long id, double timeout_s);
+
+/* Result of run id: *done = 0 while it runs; when done, its status, V-cycles
+ * summed over its steps, phi at its last step (host, n cells; nullable) and
+ * times3 = {submit, admit, done} in seconds of a monotonic clock (nullable). */
+chhs_status chhs_server_result(chhs_server_t* sv, long long id, int* done, int* status, int* vcycles,
+                               double* phi_out, double* times3);
+
+/* Forget a finished run's result. */
+chhs_status chhs_server_release(chhs_server_t* sv, long long id);
+
+/* Runs waiting, on the GPU and finished, and pool bytes in use (each nullable). */
+chhs_status chhs_server_stats(chhs_server_t* sv, int* queued, int* active, int* done, size_t* pool_in_use);
+
+/* Stop the worker (runs still active are abandoned) and free everything. */
+void chhs_server_destroy(chhs_server_t* sv);
 
 /* Number of multigrid levels of the handle (finest included). */
 int chhs_num_levels(const chhs_t* run);

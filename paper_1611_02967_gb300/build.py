@@ -4,7 +4,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "chhs.cu"), os.path.join(HERE, "csrc", "chhs_noalloc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("chhs.cu", "chhs_noalloc.cu", "chhs_serve.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
                   if f.endswith((".cuh", ".h"))] + [os.path.join(ROOT, "include", "chhs.h")]
 LIB = os.path.join(HERE, "libchhs.so")

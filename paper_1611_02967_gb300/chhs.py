@@ -25,15 +25,23 @@ STATUS_NAMES = {0: "CHHS_OK", 1: "CHHS_ERR_INVALID_ARG", 2: "CHHS_ERR_OOM", 3: "
 EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_create_ext", "chhs_set_phi",
            "chhs_step", "chhs_step_async", "chhs_wait", "chhs_launch_counts", "chhs_profile_step",
            "chhs_mass", "chhs_energy", "chhs_get_phi", "chhs_get_state", "chhs_set_state",
-           "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc"]
+           "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc", "chhs_dissipation",
+           "chhs_server_create", "chhs_server_submit", "chhs_server_wait", "chhs_server_result",
+           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy"]
 
 # kernel kinds of chhs_profile_step
-K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "coarsest", "norm", "frame"]
+K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
 
 
 class chhs_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_v", ctypes.c_int),
                 ("coarsest", ctypes.c_int), ("tol", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class chhs_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("eps", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("phi0", ctypes.c_void_p), ("phi_prev", ctypes.c_void_p)]
 
 
 class ChhsError(RuntimeError):
@@ -68,6 +76,14 @@ def lib():
             "chhs_profile_step": (i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
             "chhs_mass": (i, [_vp, _dp]),
             "chhs_energy": (i, [_vp, _dp, _dp]),
+            "chhs_dissipation": (i, [_vp, _dp, _dp, _dp]),
+            "chhs_server_create": (i, [sz, i, i, ctypes.POINTER(_vp)]),
+            "chhs_server_submit": (i, [_vp, ctypes.POINTER(chhs_request), ctypes.POINTER(ctypes.c_longlong)]),
+            "chhs_server_wait": (i, [_vp, ctypes.c_longlong, d]),
+            "chhs_server_result": (i, [_vp, ctypes.c_longlong, _ip, _ip, _ip, _vp, _dp]),
+            "chhs_server_release": (i, [_vp, ctypes.c_longlong]),
+            "chhs_server_stats": (i, [_vp, _ip, _ip, _ip, ctypes.POINTER(sz)]),
+            "chhs_server_destroy": (None, [_vp]),
             "chhs_get_phi": (i, [_vp, _vp, i]),
             "chhs_get_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
             "chhs_set_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
@@ -245,6 +261,12 @@ class Run:
         self._check(lib().chhs_energy(self.handle, ctypes.byref(E), ctypes.byref(F)))
         return E.value, F.value
 
+    def dissipation(self):
+        """(||grad_h mu||^2, ||u||^2, max |div_h u|) of the last accepted step."""
+        a, b, c = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self._check(lib().chhs_dissipation(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
     def get_phi(self, out=None):
         if out is None:
             out = np.empty(self.shape)
@@ -265,3 +287,77 @@ class Run:
         if len(devs) > 1:
             raise ValueError("mixed host and device buffers")
         self._check(lib().chhs_set_state(self.handle, *[b[0] for b in bufs], devs.pop()))
+
+
+class Server:
+    """The request loop of the C ABI (chhs_server_*): continuous batching of
+    independent runs on one GPU."""
+
+    def __init__(self, pool_bytes, max_active=16, steps_per_slice=5):
+        h = ctypes.c_void_p()
+        st = lib().chhs_server_create(int(pool_bytes), int(max_active), int(steps_per_slice), ctypes.byref(h))
+        if st != CHHS_OK:
+            raise ChhsError(st, "chhs_server_create failed")
+        self.handle = h
+        self.shapes = {}
+
+    def submit(self, shape, h, eps, gamma, dt, nsteps, phi0, precision=0, phi_prev=None):
+        shape = tuple(int(x) for x in shape)
+        n = int(np.prod(shape))
+        dim, nn = _dims(shape)
+        p0, dev0, k0 = _buf(phi0, n)
+        p1, dev1, k1 = _buf(phi_prev, n)
+        if dev0 or dev1:
+            raise ValueError("server requests take host arrays")
+        r = chhs_request(dim, nn, float(h), float(eps), float(gamma), float(dt), int(nsteps), int(precision),
+                         p0, p1)
+        rid = ctypes.c_longlong(0)
+        st = lib().chhs_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid))
+        if st != CHHS_OK:
+            raise ChhsError(st, "chhs_server_submit failed")
+        self.shapes[rid.value] = shape
+        return rid.value
+
+    def wait(self, rid, timeout=60.0):
+        return lib().chhs_server_wait(self.handle, ctypes.c_longlong(rid), float(timeout)) == CHHS_OK
+
+    def result(self, rid, with_phi=True):
+        """dict(done, status, vcycles, phi, t_submit, t_admit, t_done) of a run."""
+        done, status, v = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        times = (ctypes.c_double * 3)()
+        phi = np.empty(self.shapes[rid]) if with_phi else None
+        st = lib().chhs_server_result(self.handle, ctypes.c_longlong(rid), ctypes.byref(done), ctypes.byref(status),
+                                      ctypes.byref(v), ctypes.c_void_p(phi.ctypes.data) if with_phi else None, times)
+        if st != CHHS_OK:
+            raise ChhsError(st, "chhs_server_result failed")
+        if not done.value:
+            return dict(done=False)
+        return dict(done=True, status=status.value, vcycles=v.value, phi=phi, t_submit=times[0],
+                    t_admit=times[1], t_done=times[2])
+
+    def release(self, rid):
+        lib().chhs_server_release(self.handle, ctypes.c_longlong(rid))
+        self.shapes.pop(rid, None)
+
+    def stats(self):
+        q, a, d = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        used = ctypes.c_size_t(0)
+        lib().chhs_server_stats(self.handle, ctypes.byref(q), ctypes.byref(a), ctypes.byref(d), ctypes.byref(used))
+        return dict(queued=q.value, active=a.value, done=d.value, pool_in_use=used.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().chhs_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -473,6 +473,16 @@ struct Enqueue {
     return CHHS_OK;
   }
 
+  static chhs_status dissipation(chhs_t* run) {
+    const int nb = nblocks(run->ncell());
+    k_dissip_partial<DIM><<<nb, kBlock, 0, run->stream>>>(run->lev[0], run->gamma, 1.0 / run->h, run->partials);
+    k_dissip_finish<<<1, 32, 0, run->stream>>>(run->partials, nb, run->st);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(run->host_st, run->st, sizeof(DevState), cudaMemcpyDeviceToHost, run->stream));
+    CU(cudaStreamSynchronize(run->stream));
+    return CHHS_OK;
+  }
+
   static chhs_status energy(chhs_t* run) {
     const int nx = run->n[0], ny = run->n[1], nz = run->n[2];
     const int nb = nblocks(run->ncell());
@@ -776,6 +786,19 @@ chhs_status chhs_energy(chhs_t* run, double* E_out, double* F_out) {
   *E_out = E;
   // Eq. 2.9: F_h = E_h + 1/4 ||phi - psi||^2 + 1/8 eps^2 ||grad_h(phi - psi)||^2
   if (F_out) *F_out = E + 0.25 * hd * d[4] + 0.125 * e2 * hd * d[5];
+  return CHHS_OK;
+}
+
+chhs_status chhs_dissipation(chhs_t* run, double* grad_mu_sq, double* u_sq, double* div_u_max) {
+  if (!run) return CHHS_ERR_INVALID_ARG;
+  run->err.clear();
+  chhs_status s = run->dim == 2 ? Enqueue<2>::dissipation(run) : Enqueue<3>::dissipation(run);
+  if (s != CHHS_OK) return s;
+  const double* d = run->host_st->diag;
+  double hd = run->dim == 2 ? run->h * run->h : run->h * run->h * run->h;
+  if (grad_mu_sq) *grad_mu_sq = hd * d[0];
+  if (u_sq) *u_sq = hd * d[1];
+  if (div_u_max) *div_u_max = d[2];
   return CHHS_OK;
 }
 

@@ -927,6 +927,67 @@ __global__ void __launch_bounds__(kBlock) k_energy_partial(const double* phi, co
     for (int q = 0; q < 6; ++q) partials[blockIdx.x * 6 + q] = v[q];
 }
 
+// Dissipation terms of the last solved step (Eq. 2.23 and its proof):
+// per block the sums over interior faces of (D mu)^2 and u^2 with
+// u = -D p - gamma (A phi*) D mu (Eq. 2.3; u = 0 on boundary faces), and the
+// largest |div_h u| over the block's cells.  mu, p, phi* are the handle's.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_dissip_partial(Level<double> L, double gamma, double ih,
+                                                           double* partials) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  double dmax = 0.0;
+  if (c < L.ncell) {
+    int i, j, k;
+    cell_ijk(c, L.nx, L.ny, i, j, k);
+    const double muc = L.mu[c], pc = L.p[c], psc = L.phis[c];
+    double div = 0.0;
+    auto face = [&](int e, bool plus) {
+      double gmu = (L.mu[e] - muc) * ih;   // D mu, outward from c
+      double u = -(L.p[e] - pc) * ih - gamma * 0.5 * (psc + L.phis[e]) * gmu;
+      div += u * ih;
+      if (plus) {  // each interior face counted once, from its lower cell
+        v[0] += gmu * gmu;
+        v[1] += u * u;
+      }
+    };
+    const int sy = L.nx, sz = L.nx * L.ny;
+    if (i > 0) face(c - 1, false);
+    if (i + 1 < L.nx) face(c + 1, true);
+    if (j > 0) face(c - sy, false);
+    if (j + 1 < L.ny) face(c + sy, true);
+    if (DIM == 3) {
+      if (k > 0) face(c - sz, false);
+      if (k + 1 < L.nz) face(c + sz, true);
+    }
+    dmax = fabs(div);
+  }
+  block_sum<2>(v);
+  __shared__ double shm[32];
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = dmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) dmax = fmax(dmax, shm[w]);
+    partials[3 * blockIdx.x] = v[0];
+    partials[3 * blockIdx.x + 1] = v[1];
+    partials[3 * blockIdx.x + 2] = dmax;
+  }
+}
+
+static __global__ void k_dissip_finish(const double* partials, int nparts, DevState* st) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0, m = 0.0;
+  for (int q = 0; q < nparts; ++q) {
+    a += partials[3 * q];
+    b += partials[3 * q + 1];
+    m = fmax(m, partials[3 * q + 2]);
+  }
+  st->diag[0] = a;
+  st->diag[1] = b;
+  st->diag[2] = m;
+}
+
 static __global__ void k_energy_finish(const double* partials, int nparts, DevState* st) {
   double tot[6];
   sum_partials<6>(partials, nparts, tot);

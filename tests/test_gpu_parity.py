@@ -177,3 +177,37 @@ def test_invalid_arguments_rejected():
     with pytest.raises(chhs.ChhsError):
         chhs.Run((16, 16), 0.1, 0.05, -1.0, 0.01)
     assert chhs.workspace_bytes((512, 512)) > 11 * 512 * 512 * 8
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape,h,eps,gamma,dt", [((64, 64), 0.05, 0.05, 1.0, 0.01),
+                                                  ((16, 16, 16), 0.1, 0.1, 2.0, 0.005)])
+def test_dissipation_and_discrete_energy_law(shape, h, eps, gamma, dt, precision):
+    """The GPU's dissipation terms match the oracle's on the same fields, and the
+    GPU's own steps satisfy the exact discrete energy law behind Eq. 2.23:
+    F_h(phi^{m+1},phi^m) - F_h(phi^m,phi^{m-1}) + 1/4||a-b||^2 + 1/8 eps^2||grad(a-b)||^2
+    + s||grad mu||^2 + (s/gamma)||u||^2 = 0 up to the solver residual
+    (a = phi^{m+1} - phi^m, b = phi^m - phi^{m-1})."""
+    phi0 = inputs.spinodal(shape, 91, mean=0.0, amplitude=0.4)
+    with _run(shape, h, eps, gamma, dt, precision) as run:
+        run.set_phi(phi0)
+        run.step(2)
+        for _ in range(3):
+            phim, phimm1, _, _ = run.get_state()
+            _, F0 = run.energy()
+            run.step(1)
+            phip, _, mu, p = run.get_state()
+            _, F1 = run.energy()
+            gmu, u2, divmax = run.dissipation()
+            phis = 1.5 * phim - 0.5 * phimm1
+            o_u2, o_div = oracle.velocity(phis, mu, p, h, gamma)
+            o_gmu = oracle.grad_inner(mu, mu, h)
+            assert abs(gmu - o_gmu) <= 1e-12 * max(1.0, o_gmu)
+            assert abs(u2 - o_u2) <= 1e-12 * max(1.0, o_u2)
+            assert abs(divmax - np.max(np.abs(o_div))) <= 1e-9
+            assert divmax < 1e-6  # div_h u = 0 up to the residual (r_p scaled by 1/h-ish)
+            a, b = phip - phim, phim - phimm1
+            slack = 0.25 * oracle.inner(a - b, a - b, h) + 0.125 * eps ** 2 * oracle.grad_inner(a - b, a - b, h)
+            terms = (F1 - F0, slack, dt * gmu, dt / gamma * u2)
+            law = sum(terms)
+            assert abs(law) <= 1e-7 * max(abs(t) for t in terms), terms
