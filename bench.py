@@ -72,8 +72,13 @@ def config(world):
 
 
 def kernel_hash():
+    """Hash of the part of the kernel header that defines k_smooth and what it
+    calls (everything before the transfer kernels), so that edits to other
+    kernels do not invalidate the smoother's recorded traffic."""
     with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        src = f.read()
+    cut = src.find(b"// ---------------------------------------------------------------- transfers")
+    return hashlib.sha256(src[:cut if cut > 0 else len(src)]).hexdigest()[:16]
 
 
 def measured_traffic():
@@ -206,7 +211,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(1),
+            "data": "synthetic", "config": dict(config(1), l2="not applicable (host CPU)"),
             "vcycles_per_step": sum(vs) / len(vs),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -268,7 +268,8 @@ struct Enqueue {
     for (int it = 0; it < sweeps; ++it)
       for (int colour = 0; colour < 2; ++colour) {
         const int with_rhs = (rhs && it == 0) ? 1 : 0;
-        launch(run, s, L.ncell == run->ncell() ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, colour_cells(L, colour), [&] {
+        const int kind = L.ncell == run->ncell() ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH;
+        launch(run, s, kind, colour_cells(L, colour), [&] {
           pdl(k_smooth<T, DIM, CORR>, blocks, kSmoothBlock, s, L, K, colour, with_rhs);
         });
       }
