@@ -310,6 +310,53 @@ def served_leg(capacity_cell_steps_per_s, seed=5, nruns=40):
             "vcycles_per_step": float(sum(r["vcycles"] for r in res) / steps.sum()), "sample": SERVED_DESC}
 
 
+def bubbles_leg(stream, flush, steps=10, warmup=3):
+    """The 128^3 bubble workload (3D, eps 0.04, gamma 2, dt 0.005): both forms,
+    device-timed like the main line, from the same state after warm-up."""
+    from paper_1611_02967_gb300 import chhs, inputs
+    w = inputs.workload("bubbles128")
+    out = {"workload": "3D bubbles 128^3 on (0,6.4)^3, eps 0.04, gamma 2, dt 0.005, 8 tanh bubbles (seed 3)",
+           "steps": steps}
+    state = None
+    for prec, key in ((0, "f64"), (1, "mixed")):
+        run = chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream,
+                       opts=chhs.default_opts(precision=prec))
+        run.set_phi(w["phi0"])
+        if state is None:
+            run.step(warmup)
+            state = run.get_state()
+        run.set_state(*state)
+        ms, v, r = time_steps(run, steps, stream, flush)
+        out[key] = {"value": 128 ** 3 * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                    "vcycles_per_step": v / steps, "final_resid": r}
+        run.close()
+    return out
+
+
+def batched_leg(seed=4, nruns=32, steps=20):
+    """A sample of the batched workload (runs of sizes {64..1024}^2, eps
+    U(0.02,0.08), gamma U(0.5,4), dt 0.005, mixed precision) submitted at once
+    to the request loop; aggregate cell-steps/s."""
+    import numpy as np
+
+    from paper_1611_02967_gb300 import chhs, inputs
+    u = inputs.uniform01(seed, nruns * 3, stream=13).reshape(nruns, 3)
+    sizes = np.array([64, 128, 256, 512, 1024])[np.minimum((u[:, 0] * 5).astype(int), 4)]
+    phis = [inputs.spinodal((int(n), int(n)), seed * 1000 + k, mean=0.0) for k, n in enumerate(sizes)]
+    with chhs.Server(pool_bytes=8 << 30, max_active=32, steps_per_slice=5) as sv:
+        ids = [sv.submit((int(n), int(n)), 0.025, 0.02 + 0.06 * u[k, 1], 0.5 + 3.5 * u[k, 2], 0.005, steps,
+                         phis[k], precision=1) for k, n in enumerate(sizes)]
+        for rid in ids:
+            sv.wait(rid, 600.0)
+        res = [sv.result(rid, with_phi=False) for rid in ids]
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    work = float((sizes.astype(float) ** 2).sum() * steps)
+    return {"value": work / span, "unit": UNIT, "runs": nruns, "steps_each": steps, "seconds": span,
+            "all_converged": all(r["status"] == 0 for r in res),
+            "sample": "%d of the 256 runs (sizes {64..1024}^2, seed 4), %d steps each, all submitted at "
+                      "t = 0 to the request loop (32 slots, mixed precision)" % (nruns, steps)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -413,6 +460,8 @@ def run_ours(args):
     run32.close()
 
     served = served_leg(mixed["value"] / world)
+    batched = batched_leg()
+    bubbles = bubbles_leg(stream, flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -426,7 +475,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config(world), "vcycles_per_step": vtot / args.steps, "final_resid": resid,
-                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "mixed": mixed, "served": served, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "mixed": mixed, "served": served, "batched": batched, "bubbles128": bubbles,
+                "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
