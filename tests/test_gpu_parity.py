@@ -211,3 +211,20 @@ def test_dissipation_and_discrete_energy_law(shape, h, eps, gamma, dt, precision
             terms = (F1 - F0, slack, dt * gmu, dt / gamma * u2)
             law = sum(terms)
             assert abs(law) <= 1e-7 * max(abs(t) for t in terms), terms
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("nu1,nu2,coarsest", [(1, 1, 2), (0, 2, 2), (2, 0, 2), (3, 1, 2), (2, 2, 8)])
+@pytest.mark.parametrize("shape", [(64, 64), (32, 16, 16)])
+def test_solver_options_reach_the_same_answer(shape, nu1, nu2, coarsest, precision):
+    """Other V(nu1, nu2) cycles and a coarser stopping grid take other code
+    paths (a separate coarse right-hand side when nu1 = 0, tiles with no
+    passes, a longer coarse tail); they must converge to the same step."""
+    h, eps, gamma, dt = 0.05, 0.05, 2.0, 0.01
+    phi0 = inputs.spinodal(shape, 33, mean=0.0, amplitude=0.4)
+    opts = chhs.default_opts(precision=precision, nu1=nu1, nu2=nu2, coarsest=coarsest, max_v=200)
+    with chhs.Run(shape, h, eps, gamma, dt, opts=opts) as run:
+        run.set_phi(phi0)
+        run.step(2)
+        for _ in range(2):
+            _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
