@@ -97,11 +97,13 @@ chhs_status chhs_step(chhs_t* run, int nsteps, int* vcycles_out, double* resid_o
 
 /* The asynchronous half of chhs_step: enqueue nsteps steps on the handle's
  * stream and return without waiting.  The caller may record events around
- * it.  Call chhs_wait before any other call on the handle. */
+ * it, and may call it several times before one chhs_wait: the steps of all
+ * those calls count together.  Call chhs_wait before any other call on the
+ * handle. */
 chhs_status chhs_step_async(chhs_t* run, int nsteps);
 
-/* Wait for the steps enqueued by chhs_step_async; outputs and status as
- * chhs_step. */
+/* Wait for the steps enqueued by chhs_step_async since the last wait;
+ * outputs (summed over those steps) and status as chhs_step. */
 chhs_status chhs_wait(chhs_t* run, int* vcycles_out, double* resid_out);
 
 /* Kernel launches of one time step's graph: *per_vcycle for each V-cycle and

@@ -167,6 +167,7 @@ struct chhs {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches_per_v = 0, launches_per_step = 0;
+  bool pending = false;  // steps enqueued by chhs_step_async since the last chhs_wait
   int* counter = nullptr;  // counts launches while the graph is captured
   Prof* prof = nullptr;  // per-launch events while profiling
   std::string err;
@@ -705,14 +706,18 @@ chhs_status chhs_step_async(chhs_t* run, int nsteps) {
   if (!run) return CHHS_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(run, CHHS_ERR_INVALID_ARG, "nsteps < 0");
   run->err.clear();
-  k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, run->opts.max_v);
-  CU(cudaGetLastError());
+  if (!run->pending) {  // the first call since the last wait starts a new count
+    k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, run->opts.max_v);
+    CU(cudaGetLastError());
+    run->pending = true;
+  }
   for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(run->exec, run->stream));
   return CHHS_OK;
 }
 
 chhs_status chhs_wait(chhs_t* run, int* vcycles_out, double* resid_out) {
   if (!run) return CHHS_ERR_INVALID_ARG;
+  run->pending = false;
   CU(cudaMemcpyAsync(run->host_st, run->st, sizeof(DevState), cudaMemcpyDeviceToHost, run->stream));
   CU(cudaStreamSynchronize(run->stream));
   const DevState& h = *run->host_st;

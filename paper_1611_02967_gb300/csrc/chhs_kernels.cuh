@@ -764,11 +764,12 @@ __device__ __forceinline__ void tail_prolong(const Level<T>& F, const Level<T>& 
 }
 
 // The coarsest grid: red-black sweeps until the residual has fallen by 1e-6
-// (ample for a coarse-grid correction inside a V-cycle that contracts by
-// ~0.1), or, after the first 8 sweeps, stops falling (the arithmetic's floor;
-// early sweeps of this coupled system may raise the residual before it
-// falls), or after 2000 sweeps.  A slowly contracting solve (a large coarsest
-// grid) keeps sweeping.
+// in double precision or 1e-4 in single (either is ample for a coarse-grid
+// correction inside a V-cycle that contracts by ~0.1, and the single-precision
+// target stays above that arithmetic's floor), or, after the first 8 sweeps,
+// stops falling (the floor; early sweeps of this coupled system may raise the
+// residual before it falls), or after 2000 sweeps.  A slowly contracting
+// solve (a large coarsest grid) keeps sweeping.
 template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>& K) {
   __shared__ double sh_r;
@@ -790,7 +791,8 @@ __device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>
     double r = sh_r;
     __syncthreads();
     if (r0 < 0.0) r0 = r;
-    if (!(r > 1e-6 * r0) || r < 1e-300) break;
+    const double target = sizeof(T) == 8 ? 1e-6 : 1e-4;
+    if (!(r > target * r0) || r < 1e-300) break;
     if (it >= 8 && r >= prev) break;
     prev = r;
     for (int colour = 0; colour < 2; ++colour) tail_smooth<T, DIM, CORR>(L, K, colour, false);
