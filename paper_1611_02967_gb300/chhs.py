@@ -27,7 +27,7 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_mass", "chhs_energy", "chhs_get_phi", "chhs_get_state", "chhs_set_state",
            "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc", "chhs_dissipation",
            "chhs_server_create", "chhs_server_submit", "chhs_server_wait", "chhs_server_result",
-           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy"]
+           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
@@ -84,6 +84,7 @@ def lib():
             "chhs_server_release": (i, [_vp, ctypes.c_longlong]),
             "chhs_server_stats": (i, [_vp, _ip, _ip, _ip, ctypes.POINTER(sz)]),
             "chhs_server_destroy": (None, [_vp]),
+            "chhs_profile_smooth": (i, [_vp, i, _dp]),
             "chhs_get_phi": (i, [_vp, _vp, i]),
             "chhs_get_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
             "chhs_set_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
@@ -249,6 +250,13 @@ class Run:
             acc[k][1] += la[q]
             acc[k][2] += un[q]
         return acc
+
+    def profile_smooth(self, npasses=100):
+        """Average ms of one finest-level double-precision smoother pass, timed
+        back to back (call after a converged step)."""
+        ms = ctypes.c_double(0.0)
+        self._check(lib().chhs_profile_smooth(self.handle, int(npasses), ctypes.byref(ms)))
+        return ms.value
 
     def mass(self):
         m = ctypes.c_double(0.0)

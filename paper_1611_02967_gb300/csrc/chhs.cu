@@ -56,9 +56,9 @@ std::vector<Shape> level_shapes(int dim, const int n[3], int coarsest) {
 }
 
 // Per-level fields: phi mu p fphi fmu fp phim phis phi0 mu0 p0, ax ay Mx My,
-// sM sa, cAe cCD cG (+ az Mz in 3D), and in single precision also phi_b.
+// sM sa, cAe cC cGn cHn cQ (+ az Mz in 3D), and in single precision also phi_b.
 constexpr int kBaseFields = 11;
-int level_fields(int dim, bool single) { return kBaseFields + (dim == 3 ? 11 : 9) + (single ? 1 : 0); }
+int level_fields(int dim, bool single) { return kBaseFields + (dim == 3 ? 13 : 11) + (single ? 1 : 0); }
 
 // Levels with at most this many cells run inside the one-block tail kernel.
 // In double precision one SM does 2 FMA per clock and a single warp's
@@ -512,7 +512,7 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   size_t nc = (size_t)sh.n[0] * sh.n[1] * sh.n[2];
   size_t stride = align_up(sizeof(T) * nc);
   const int nf = level_fields(run->dim, single);
-  T* f[kBaseFields + 12];
+  T* f[kBaseFields + 14];
   for (int q = 0; q < nf; ++q) f[q] = reinterpret_cast<T*>(base + q * stride);
   const double hl = run->h * double(1 << l);
   Level<T> L;
@@ -522,8 +522,8 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   L.phi0 = f[8]; L.mu0 = f[9]; L.p0 = f[10];
   L.ax = f[11]; L.ay = f[12]; L.Mx = f[13]; L.My = f[14];
   L.sM = f[15]; L.sa = f[16];
-  L.cAe = f[17]; L.cCD = f[18]; L.cG = f[19];
-  int q = 20;
+  L.cAe = f[17]; L.cC = f[18]; L.cGn = f[19]; L.cHn = f[20]; L.cQ = f[21];
+  int q = 22;
   L.az = run->dim == 3 ? f[q++] : nullptr;
   L.Mz = run->dim == 3 ? f[q++] : nullptr;
   L.phib = single ? f[q++] : nullptr;
@@ -767,6 +767,51 @@ chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_o
     units_out[prof.kind[q]] += prof.units[q];
   }
   return chhs_wait(run, nullptr, nullptr);
+}
+
+chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass) {
+  if (!run || npasses < 1 || !ms_per_pass) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
+  if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
+  run->err.clear();
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  const Level<double>& L = run->lev[0];
+  const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
+  const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
+  const Coefs<double> K{run->dt, run->gamma, 0.75 * run->eps * run->eps};
+  // the passes overwrite (phi, mu, p) of the finest level: keep a copy and put it back
+  const size_t bytes = sizeof(double) * (size_t)L.ncell;
+  double* keep = nullptr;
+  if (cudaMalloc(&keep, 3 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return fail(run, CHHS_ERR_OOM, "cudaMalloc failed");
+  }
+  CU(cudaMemcpyAsync(keep, L.phi, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(keep + L.ncell, L.mu, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(keep + 2 * (size_t)L.ncell, L.p, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  // one untimed pass, then npasses timed ones back to back
+  for (int k = 0; k <= npasses; ++k) {
+    if (k == 1) CU(cudaEventRecord(a, run->stream));
+    if (run->dim == 2)
+      pdl(k_smooth<double, 2, false>, blocks, kSmoothBlock, run->stream, L, K, k & 1, 0);
+    else
+      pdl(k_smooth<double, 3, false>, blocks, kSmoothBlock, run->stream, L, K, k & 1, 0);
+  }
+  CU(cudaEventRecord(b, run->stream));
+  CU(cudaMemcpyAsync(L.phi, keep, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.mu, keep + L.ncell, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.p, keep + 2 * (size_t)L.ncell, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaStreamSynchronize(run->stream));
+  cudaFree(keep);
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms_per_pass = ms / npasses;
+  return CHHS_OK;
 }
 
 chhs_status chhs_mass(chhs_t* run, double* mass_out) {

@@ -114,6 +114,10 @@ __device__ __forceinline__ void tile_N(const TileView<T, CORR>& V, int s, int SW
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
                                                       int halo, int rhs, int prolong, int restrict_out) {
+  // The tiles serve the correction-form (single-precision) levels only: the
+  // plain form's right-hand side f_mu carries the shift of cubic_P, which
+  // tile_N does not.
+  static_assert(CORR, "k_tile runs the correction form only");
   pdl_enter();
   extern __shared__ __align__(16) unsigned char tile_smem[];
   const int SW = kTileW + 2 * halo, SH = kTileH + 2 * halo, SN = SW * SH;

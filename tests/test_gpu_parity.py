@@ -228,3 +228,18 @@ def test_solver_options_reach_the_same_answer(shape, nu1, nu2, coarsest, precisi
         run.step(2)
         for _ in range(2):
             _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+
+
+def test_profile_smooth_keeps_state():
+    """The smoother-timing entry point restores the finest level's fields."""
+    w = inputs.workload("spinodal64")
+    with _run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], 0) as run:
+        run.set_phi(w["phi0"])
+        run.step(2)
+        before = run.get_state()
+        ms = run.profile_smooth(10)
+        assert 0.0 < ms < 10.0
+        after = run.get_state()
+        for a, b in zip(before, after):
+            assert np.array_equal(a, b)
+        run.step(1)
