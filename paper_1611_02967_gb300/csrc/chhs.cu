@@ -529,6 +529,9 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   L.phib = single ? f[q++] : nullptr;
   L.nx = sh.n[0]; L.ny = sh.n[1]; L.nz = sh.n[2];
   L.ncell = (int)nc;
+  L.rnx = 1.0f / (float)sh.n[0];
+  L.rny = 1.0f / (float)sh.n[1];
+  L.rhw = 1.0f / (float)((sh.n[0] + 1) / 2);
   L.ih2 = T(1.0 / (hl * hl));
   L.h2 = T(hl * hl);
   L.sih2 = T(run->dt / (hl * hl));

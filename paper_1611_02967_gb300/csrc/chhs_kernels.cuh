@@ -46,6 +46,7 @@ struct Level {
   T *cAe, *cC, *cGn, *cHn, *cQ;
   int nx, ny, nz;  // nz == 1 in 2D
   int ncell;
+  float rnx, rny, rhw;  // 1/nx, 1/ny, 1/ceil(nx/2) in single precision (small_div)
   T ih2, h2;       // 1/h^2 and h^2 on this level
   T sih2;          // s / h^2
   T e34ih2;        // (3/4) eps^2 / h^2
@@ -138,6 +139,22 @@ __device__ __forceinline__ void cell_ijk(int c, int nx, int ny, int& i, int& j, 
   k = r / ny;
 }
 
+// t / d for 0 <= t < 2^21 and d >= 1, given rd = 1/d rounded to single
+// precision: (t + 1/2) / d lies at least 1/(2d) from an integer, and the
+// product (t + 1/2) * rd errs by less than 2^-22 (t + 1/2) / d, which is
+// smaller for t < 2^21, so truncation gives the exact quotient.  Two
+// single-precision operations instead of an integer division.
+__device__ __forceinline__ int small_div(int t, float rd) { return __float2int_rz((float(t) + 0.5f) * rd); }
+
+// cell_ijk for levels of fewer than 2^21 cells (the tail's levels).
+template <typename T>
+__device__ __forceinline__ void cell_ijk_small(int c, const Level<T>& L, int& i, int& j, int& k) {
+  const int r = small_div(c, L.rnx);
+  i = c - r * L.nx;
+  k = small_div(r, L.rny);
+  j = r - k * L.ny;
+}
+
 // Neighbour sums of one cell over its interior faces f (neighbour e):
 //   Mp = sum (M_f mu_e + a_f p_e), amu = sum a_f mu_e,
 //   phi = sum phi_e, p = sum p_e, m = n_c.
@@ -156,23 +173,29 @@ __device__ __forceinline__ void nb_sums(const Level<T>& L, const T* phi, const T
                                         int i, int j, int k, Nb<T>& S) {
   S.Mp = S.amu = S.phi = S.p = T(-0.0);
   S.m = 0;
-  auto face = [&](int e, T a, T M) {
-    T mue = mu[e], pe = p[e];
+  // Branch-free: a missing face reads cell c itself (a valid index) and
+  // contributes a = M = 0 and -0 to the plain sums, so all loads of a cell
+  // issue together.  The face coefficient of face f between c and e is held
+  // by the lower of the two cells (fe).
+  auto face = [&](bool in, int e, int fe, const T* af, const T* Mf) {
+    const int es = in ? e : c, fs = in ? fe : c;
+    const T mue = mu[es], pe = p[es], phie = phi[es], a0 = af[fs], M0 = Mf[fs];
+    const T a = in ? a0 : T(0), M = in ? M0 : T(0);
     S.Mp += M * mue;
     S.Mp += a * pe;
     S.amu += a * mue;
-    S.phi += phi[e];
-    S.p += pe;
-    S.m += 1;
+    S.phi += in ? phie : T(-0.0);
+    S.p += in ? pe : T(-0.0);
+    S.m += in ? 1 : 0;
   };
   const int sy = L.nx, sz = L.nx * L.ny;
-  if (i > 0) face(c - 1, L.ax[c - 1], L.Mx[c - 1]);
-  if (i + 1 < L.nx) face(c + 1, L.ax[c], L.Mx[c]);
-  if (j > 0) face(c - sy, L.ay[c - sy], L.My[c - sy]);
-  if (j + 1 < L.ny) face(c + sy, L.ay[c], L.My[c]);
+  face(i > 0, c - 1, c - 1, L.ax, L.Mx);
+  face(i + 1 < L.nx, c + 1, c, L.ax, L.Mx);
+  face(j > 0, c - sy, c - sy, L.ay, L.My);
+  face(j + 1 < L.ny, c + sy, c, L.ay, L.My);
   if (DIM == 3) {
-    if (k > 0) face(c - sz, L.az[c - sz], L.Mz[c - sz]);
-    if (k + 1 < L.nz) face(c + sz, L.az[c], L.Mz[c]);
+    face(k > 0, c - sz, c - sz, L.az, L.Mz);
+    face(k + 1 < L.nz, c + sz, c, L.az, L.Mz);
   }
 }
 
@@ -727,12 +750,13 @@ __device__ __forceinline__ void tail_smooth(const Level<T>& L, const Coefs<T>& K
   const int hw = (L.nx + 1) >> 1;
   const int total = hw * L.ny * L.nz;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int row = t / hw;
-    int ti = t - row * hw;
-    int j = row % L.ny, k = row / L.ny;
-    int i = 2 * ti + ((j + k + colour) & 1);
+    const int row = small_div(t, L.rhw);
+    const int ti = t - row * hw;
+    const int k = small_div(row, L.rny);
+    const int j = row - k * L.ny;
+    const int i = 2 * ti + ((j + k + colour) & 1);
     if (i >= L.nx) continue;
-    int c = i + L.nx * (j + L.ny * k);
+    const int c = i + L.nx * (j + L.ny * k);
     T f1, f2, f3;
     cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, rhs, f1, f2, f3);
     cell_update<T, DIM, CORR>(L, K, c, i, j, k, f1, f2, f3);
@@ -744,43 +768,59 @@ template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void tail_rhs(const Level<T>& L, const Coefs<T>& K) {
   for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
     int i, j, k;
-    cell_ijk(c, L.nx, L.ny, i, j, k);
+    cell_ijk_small(c, L, i, j, k);
     T f1, f2, f3;
     cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, true, f1, f2, f3);
   }
   __syncthreads();
 }
 
+// Residual and restriction inside the tail: one thread per fine cell, the
+// 2^d children of a coarse cell in adjacent lanes (child d = t mod 2^d), their
+// values summed by shuffles in a fixed order.  Every thread of the block
+// takes part in the shuffles (the round count is uniform).
 template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void tail_restrict(const Level<T>& F, const Level<T>& C, const Coefs<T>& K) {
+  constexpr int NCH = DIM == 3 ? 8 : 4;
+  constexpr int NV = CORR ? 7 : 6;
   const T w = DIM == 3 ? T(0.125) : T(0.25);
-  const int kz = DIM == 3 ? 2 : 1;
-  for (int q = threadIdx.x; q < C.ncell; q += blockDim.x) {
-    int I, J, KK;
-    cell_ijk(q, C.nx, C.ny, I, J, KK);
-    T r1 = 0, r2 = 0, r3 = 0, a = 0, b = 0, d = 0, e = 0;
-    for (int dk = 0; dk < kz; ++dk)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int di = 0; di < 2; ++di) {
-          int i = 2 * I + di, j = 2 * J + dj, k = 2 * KK + dk;
-          int c = i + F.nx * (j + F.ny * k);
-          T n1, n2, n3;
-          eval_N<T, DIM, CORR>(F, K, F.phi, F.mu, F.p, c, i, j, k, n1, n2, n3);
-          r1 += F.fphi[c] - n1;
-          r2 += F.fmu[c] - n2;
-          r3 += F.fp[c] - n3;
-          a += F.phi[c];
-          b += F.mu[c];
-          d += F.p[c];
-          if (CORR) e += F.phib[c];
-        }
-    C.fphi[q] = w * r1;
-    C.fmu[q] = w * r2;
-    C.fp[q] = w * r3;
-    C.phi[q] = C.phi0[q] = w * a;
-    C.mu[q] = C.mu0[q] = w * b;
-    C.p[q] = C.p0[q] = w * d;
-    if (CORR) C.phib[q] = w * e;
+  const int total = C.ncell * NCH;
+  const int rounds = (total + (int)blockDim.x - 1) / (int)blockDim.x;
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * (int)blockDim.x + (int)threadIdx.x;
+    const bool act = t < total;
+    const int q = t / NCH, d = t % NCH;
+    T v[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) v[m] = T(0);
+    if (act) {
+      int I, J, KK;
+      cell_ijk_small(q, C, I, J, KK);
+      const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * KK + (d >> 2);
+      const int c = i + F.nx * (j + F.ny * k);
+      T n1, n2, n3;
+      eval_N<T, DIM, CORR>(F, K, F.phi, F.mu, F.p, c, i, j, k, n1, n2, n3);
+      v[0] = F.fphi[c] - n1;
+      v[1] = F.fmu[c] - n2;
+      v[2] = F.fp[c] - n3;
+      v[3] = F.phi[c];
+      v[4] = F.mu[c];
+      v[5] = F.p[c];
+      if (CORR) v[NV - 1] = F.phib[c];
+    }
+#pragma unroll
+    for (int o = 1; o < NCH; o <<= 1)
+#pragma unroll
+      for (int m = 0; m < NV; ++m) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+    if (act && d == 0) {
+      C.fphi[q] = w * v[0];
+      C.fmu[q] = w * v[1];
+      C.fp[q] = w * v[2];
+      C.phi[q] = C.phi0[q] = w * v[3];
+      C.mu[q] = C.mu0[q] = w * v[4];
+      C.p[q] = C.p0[q] = w * v[5];
+      if (CORR) C.phib[q] = w * v[NV - 1];
+    }
   }
   __syncthreads();
 }
@@ -789,7 +829,7 @@ template <typename T, int DIM>
 __device__ __forceinline__ void tail_prolong(const Level<T>& F, const Level<T>& C) {
   for (int c = threadIdx.x; c < F.ncell; c += blockDim.x) {
     int i, j, k;
-    cell_ijk(c, F.nx, F.ny, i, j, k);
+    cell_ijk_small(c, F, i, j, k);
     int q = (i >> 1) + C.nx * ((j >> 1) + C.ny * (DIM == 3 ? (k >> 1) : 0));
     F.phi[c] += C.phi[q] - C.phi0[q];
     F.mu[c] += C.mu[q] - C.mu0[q];
@@ -821,7 +861,7 @@ __device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>
       T acc = T(0);
       for (int c = threadIdx.x; c < L.ncell; c += nw * 32) {
         int i, j, k;
-        cell_ijk(c, L.nx, L.ny, i, j, k);
+        cell_ijk_small(c, L, i, j, k);
         T n1, n2, n3;
         eval_N<T, DIM, CORR>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
         T r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = K.s * (L.fp[c] - n3);
@@ -883,7 +923,7 @@ __device__ __forceinline__ Level<T> tail_level(const Tail<T>& tl, int l, unsigne
 }
 
 template <typename T, int DIM, bool CORR>
-__global__ void __launch_bounds__(kTailThreads) k_tail(Tail<T> tl, Coefs<T> K) {
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(Tail<T> tl, Coefs<T> K) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char tail_smem[];
   const int n = tl.n;
