@@ -56,9 +56,13 @@ std::vector<Shape> level_shapes(int dim, const int n[3], int coarsest) {
 }
 
 // Per-level fields: phi mu p fphi fmu fp phim phis phi0 mu0 p0, ax ay Mx My,
-// sM sa, cAe cC cGn cHn cQ (+ az Mz in 3D), and in single precision also phi_b.
+// sM sa, cAe cC cGn cHn cQ (+ az Mz in 3D), in single precision also phi_b,
+// and in 2D single precision (the tiled levels) a second (phi, mu, p) and the
+// completed right-hand side.
 constexpr int kBaseFields = 11;
-int level_fields(int dim, bool single) { return kBaseFields + (dim == 3 ? 13 : 11) + (single ? 1 : 0); }
+int level_fields(int dim, bool single) {
+  return kBaseFields + (dim == 3 ? 13 : 11) + (single ? 1 + (dim == 2 ? 6 : 0) : 0);
+}
 
 // Levels with at most this many cells run inside the one-block tail kernel.
 // In double precision one SM does 2 FMA per clock and a single warp's
@@ -297,14 +301,28 @@ struct Enqueue {
       const dim3 grid((L.nx + kTileW - 1) / kTileW, (L.ny + kTileH - 1) / kTileH);
       const int nf = tile_nfields<CORR>();
       const int np1 = 2 * run->opts.nu1, np2 = 2 * run->opts.nu2;
+      // the pre-smoothing launch writes the second copy of the state (and the
+      // completed right-hand side), the post-smoothing launch reads them and
+      // writes the state back: no launch writes what its own tiles read
+      const TileOut<T> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3};
+      Level<T> Lb = L;
+      Lb.phi = L.phi2;
+      Lb.mu = L.mu2;
+      Lb.p = L.p2;
+      if (rhs) {
+        Lb.fphi = L.fc1;
+        Lb.fmu = L.fc2;
+        Lb.fp = L.fc3;
+      }
+      const TileOut<T> to_state{L.phi, L.mu, L.p, nullptr, nullptr, nullptr};
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu1, [&] {
         pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
-                 np1 + 1, rhs ? 1 : 0, 0, 1);
+                 np1 + 1, rhs ? 1 : 0, 0, 1, to_copy);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu2, [&] {
-        pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np2, nf, sizeof(T)), s, L, C, K, np2, np2,
-                 0, 1, 0);
+        pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np2, nf, sizeof(T)), s, Lb, C, K, np2, np2,
+                 0, 1, 0, to_state);
       });
       return;
     }
@@ -512,7 +530,7 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   size_t nc = (size_t)sh.n[0] * sh.n[1] * sh.n[2];
   size_t stride = align_up(sizeof(T) * nc);
   const int nf = level_fields(run->dim, single);
-  T* f[kBaseFields + 14];
+  T* f[kBaseFields + 20];
   for (int q = 0; q < nf; ++q) f[q] = reinterpret_cast<T*>(base + q * stride);
   const double hl = run->h * double(1 << l);
   Level<T> L;
@@ -527,6 +545,13 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   L.az = run->dim == 3 ? f[q++] : nullptr;
   L.Mz = run->dim == 3 ? f[q++] : nullptr;
   L.phib = single ? f[q++] : nullptr;
+  const bool tiles = single && run->dim == 2;
+  L.phi2 = tiles ? f[q++] : nullptr;
+  L.mu2 = tiles ? f[q++] : nullptr;
+  L.p2 = tiles ? f[q++] : nullptr;
+  L.fc1 = tiles ? f[q++] : nullptr;
+  L.fc2 = tiles ? f[q++] : nullptr;
+  L.fc3 = tiles ? f[q++] : nullptr;
   L.nx = sh.n[0]; L.ny = sh.n[1]; L.nz = sh.n[2];
   L.ncell = (int)nc;
   L.rnx = 1.0f / (float)sh.n[0];

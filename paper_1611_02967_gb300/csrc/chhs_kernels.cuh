@@ -37,6 +37,8 @@ struct Level {
   T *fphi, *fmu, *fp;  // right-hand sides
   T *phim, *phis;      // phi^m and phi* restricted to this level (fixed in a step)
   T *phib;             // correction form only: phi-part of the base state
+  T *phi2, *mu2, *p2;  // 2D single precision only: the tiles' second copy of (phi, mu, p)
+  T *fc1, *fc2, *fc3;  // ... and the completed FAS right-hand side (k_tile)
   T *phi0, *mu0, *p0;  // restricted iterate R u kept for the FAS correction
   // Coefficients fixed for a time step (k_coef): a = A_h phi* and M(a) on the
   // +x, +y (+z) face of every cell (zero on boundary faces), their sums over a
@@ -383,10 +385,16 @@ template <typename T, int DIM, bool CORR>
 __global__ void __launch_bounds__(kSmoothBlock) k_smooth(Level<T> L, Coefs<T> K, int colour, int rhs) {
   pdl_enter();
   const int hw = (L.nx + 1) >> 1;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = t / hw;
-  int ti = t - row * hw;
-  int j = row % L.ny, k = row / L.ny;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int row, k;
+  if (t < (1 << 21)) {
+    row = small_div(t, L.rhw);
+    k = small_div(row, L.rny);
+  } else {
+    row = t / hw;
+    k = row / L.ny;
+  }
+  const int ti = t - row * hw, j = row - k * L.ny;
   if (k >= L.nz) return;
   int i = 2 * ti + ((j + k + colour) & 1);
   if (i >= L.nx) return;

@@ -22,6 +22,13 @@
 //               its restriction: u_c = u_c^0 = R u, f_c = R r, phi_b,c = R phi_b.
 // The per-step face coefficients are recomputed from phi* in shared memory
 // (cheap in single precision) instead of being read from global memory.
+//
+// A tile reads its halo from global memory while other tiles of the same
+// launch write their results, so a launch never writes the arrays it reads:
+// the pre-smoothing launch reads (phi, mu, p) and f and writes the second
+// copy (phi2, mu2, p2) and the completed right-hand side (fc); the
+// post-smoothing launch reads those and writes (phi, mu, p).  (Blocks of a
+// launch are not all resident at once when other work shares the GPU.)
 #pragma once
 #include "chhs_kernels.cuh"
 
@@ -51,14 +58,11 @@ template <typename T>
 __device__ __forceinline__ void local_coef(const T* ps, int s, int SW, int i, int j, int nx, int ny,
                                            const Level<T>& L, const Coefs<T>& K, LocalCoef<T>& C) {
   const T pc = ps[s];
+  // branch-free: a missing face reads the cell itself and gets a = M = 0
   auto face = [&](bool inside, int e, T& a, T& M) {
-    if (inside) {
-      a = T(0.5) * (pc + ps[e]);
-      M = T(1) + K.gamma * a * a;
-    } else {
-      a = T(0);
-      M = T(0);
-    }
+    const T af = T(0.5) * (pc + ps[inside ? e : s]);
+    a = inside ? af : T(0);
+    M = inside ? T(1) + K.gamma * af * af : T(0);
   };
   face(i > 0, s - 1, C.aW, C.MW);
   face(i + 1 < nx, s + 1, C.aE, C.ME);
@@ -73,6 +77,13 @@ __device__ __forceinline__ void local_coef(const T* ps, int s, int SW, int i, in
   C.G = K.gamma * L.ih2 * C.sa;
 }
 
+// Where a tile launch writes its interior: (phi, mu, p) and, with rhs, the
+// completed right-hand side.
+template <typename T>
+struct TileOut {
+  T *phi, *mu, *p, *f1, *f2, *f3;
+};
+
 // Shared-memory views of one tile's fields.
 template <typename T, bool CORR>
 struct TileView {
@@ -85,14 +96,15 @@ __device__ __forceinline__ void tile_N(const TileView<T, CORR>& V, int s, int SW
                                        const Level<T>& L, const Coefs<T>& K, const LocalCoef<T>& C, T& n1, T& n2,
                                        T& n3) {
   T Mmu = 0, ap = 0, amu = 0, sphi = 0, sp = 0;
+  // branch-free: a missing face (a = M = 0 from local_coef) reads the cell itself
   auto face = [&](bool inside, int e, T a, T M) {
-    if (!inside) return;
-    T mue = V.mu[e], pe = V.p[e];
+    const int es = inside ? e : s;
+    const T mue = V.mu[es], pe = V.p[es], phie = V.phi[es];
     Mmu += M * mue;
     ap += a * pe;
     amu += a * mue;
-    sphi += V.phi[e];
-    sp += pe;
+    sphi += inside ? phie : T(0);
+    sp += inside ? pe : T(0);
   };
   face(i > 0, s - 1, C.aW, C.MW);
   face(i + 1 < nx, s + 1, C.aE, C.ME);
@@ -113,7 +125,8 @@ __device__ __forceinline__ void tile_N(const TileView<T, CORR>& V, int s, int SW
 
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
-                                                      int halo, int rhs, int prolong, int restrict_out) {
+                                                      int halo, int rhs, int prolong, int restrict_out,
+                                                      TileOut<T> out) {
   // The tiles serve the correction-form (single-precision) levels only: the
   // plain form's right-hand side f_mu carries the shift of cubic_P, which
   // tile_N does not.
@@ -132,9 +145,11 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
   const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;  // tile origin (global)
   const int gx0 = tx0 - halo, gy0 = ty0 - halo;                      // shared-memory origin (global)
 
-  // load the tile and its halo (cells outside the domain are never read)
+  // load the tile and its halo (cells outside the domain are never read);
+  // thread-to-cell maps use small_div (every index here is below 2^21)
+  const float rSW = __frcp_rn((float)SW);
   for (int s = threadIdx.x; s < SN; s += blockDim.x) {
-    int sy = s / SW, sx = s - sy * SW;
+    int sy = small_div(s, rSW), sx = s - sy * SW;
     int i = gx0 + sx, j = gy0 + sy;
     if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
     int c = i + nx * j;
@@ -169,8 +184,10 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
     int x0, x1, y0, y1;
     region(halo - 1, x0, x1, y0, y1);
     const int w = x1 - x0, total = w * (y1 - y0);
+    const float rw = __frcp_rn((float)w);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int j = y0 + t / w, i = x0 + t % w;
+      const int q = small_div(t, rw);
+      int j = y0 + q, i = x0 + (t - q * w);
       int s = (i - gx0) + SW * (j - gy0);
       LocalCoef<T> C;
       local_coef(V.phis, s, SW, i, j, nx, ny, L, K, C);
@@ -188,9 +205,11 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
     int x0, x1, y0, y1;
     region(halo - k, x0, x1, y0, y1);
     const int hw = (x1 - x0 + 1) >> 1, total = hw * (y1 - y0);
+    const float rhw = __frcp_rn((float)hw);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int j = y0 + t / hw;
-      int i = x0 + 2 * (t % hw);
+      const int q = small_div(t, rhw);
+      int j = y0 + q;
+      int i = x0 + 2 * (t - q * hw);
       i += (i + j + colour) & 1;
       if (i >= x1) continue;
       int s = (i - gx0) + SW * (j - gy0);
@@ -217,50 +236,65 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
     int x0, x1, y0, y1;
     region(0, x0, x1, y0, y1);
     const int w = x1 - x0, total = w * (y1 - y0);
+    const float rw = __frcp_rn((float)w);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int j = y0 + t / w, i = x0 + t % w;
+      const int q = small_div(t, rw);
+      int j = y0 + q, i = x0 + (t - q * w);
       int s = (i - gx0) + SW * (j - gy0), c = i + nx * j;
-      L.phi[c] = V.phi[s];
-      L.mu[c] = V.mu[s];
-      L.p[c] = V.p[s];
+      out.phi[c] = V.phi[s];
+      out.mu[c] = V.mu[s];
+      out.p[c] = V.p[s];
       if (rhs) {
-        L.fphi[c] = V.f1[s];
-        L.fmu[c] = V.f2[s];
-        L.fp[c] = V.f3[s];
+        out.f1[c] = V.f1[s];
+        out.f2[c] = V.f2[s];
+        out.f3[c] = V.f3[s];
       }
     }
   }
 
-  if (restrict_out) {  // residual on the tile and its restriction (coarse cell per thread)
-    const int cw = kTileW / 2, chh = kTileH / 2;
-    for (int t = threadIdx.x; t < cw * chh; t += blockDim.x) {
-      const int I = (tx0 >> 1) + t % cw, J = (ty0 >> 1) + t / cw;
-      if (I >= Cl.nx || J >= Cl.ny) continue;
-      T r1 = 0, r2 = 0, r3 = 0, a = 0, b = 0, d = 0, e = 0;
-      for (int dj = 0; dj < 2; ++dj)
-        for (int di = 0; di < 2; ++di) {
-          const int i = 2 * I + di, j = 2 * J + dj;
-          const int s = (i - gx0) + SW * (j - gy0);
-          LocalCoef<T> C;
-          local_coef(V.phis, s, SW, i, j, nx, ny, L, K, C);
-          T n1, n2, n3;
-          tile_N<T, CORR>(V, s, SW, i, j, nx, ny, L, K, C, n1, n2, n3);
-          r1 += V.f1[s] - n1;
-          r2 += V.f2[s] - n2;
-          r3 += V.f3[s] - n3;
-          a += V.phi[s];
-          b += V.mu[s];
-          d += V.p[s];
-          if (CORR) e += V.phib[s];
-        }
-      const int q = I + Cl.nx * J;
-      Cl.fphi[q] = T(0.25) * r1;
-      Cl.fmu[q] = T(0.25) * r2;
-      Cl.fp[q] = T(0.25) * r3;
-      Cl.phi[q] = Cl.phi0[q] = T(0.25) * a;
-      Cl.mu[q] = Cl.mu0[q] = T(0.25) * b;
-      Cl.p[q] = Cl.p0[q] = T(0.25) * d;
-      if (CORR) Cl.phib[q] = T(0.25) * e;
+  if (restrict_out) {
+    // residual on the tile and its restriction: one thread per fine cell,
+    // the four children of a coarse cell in adjacent lanes (child d = t mod 4),
+    // summed by shuffles in a fixed order; the round count is uniform so
+    // every thread takes part in the shuffles
+    constexpr int NV = CORR ? 7 : 6;
+    const int cw = kTileW / 2, chh = kTileH / 2, total = 4 * cw * chh;
+    for (int r = 0; r < total; r += blockDim.x) {
+      const int t = r + threadIdx.x, qq = t >> 2, d = t & 3;
+      const int I = (tx0 >> 1) + qq % cw, J = (ty0 >> 1) + qq / cw;
+      const bool act = t < total && I < Cl.nx && J < Cl.ny;
+      T v[NV];
+#pragma unroll
+      for (int m = 0; m < NV; ++m) v[m] = T(0);
+      if (act) {
+        const int i = 2 * I + (d & 1), j = 2 * J + (d >> 1);
+        const int s = (i - gx0) + SW * (j - gy0);
+        LocalCoef<T> C;
+        local_coef(V.phis, s, SW, i, j, nx, ny, L, K, C);
+        T n1, n2, n3;
+        tile_N<T, CORR>(V, s, SW, i, j, nx, ny, L, K, C, n1, n2, n3);
+        v[0] = V.f1[s] - n1;
+        v[1] = V.f2[s] - n2;
+        v[2] = V.f3[s] - n3;
+        v[3] = V.phi[s];
+        v[4] = V.mu[s];
+        v[5] = V.p[s];
+        if (CORR) v[NV - 1] = V.phib[s];
+      }
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+      if (act && d == 0) {
+        const int q = I + Cl.nx * J;
+        Cl.fphi[q] = T(0.25) * v[0];
+        Cl.fmu[q] = T(0.25) * v[1];
+        Cl.fp[q] = T(0.25) * v[2];
+        Cl.phi[q] = Cl.phi0[q] = T(0.25) * v[3];
+        Cl.mu[q] = Cl.mu0[q] = T(0.25) * v[4];
+        Cl.p[q] = Cl.p0[q] = T(0.25) * v[5];
+        if (CORR) Cl.phib[q] = T(0.25) * v[NV - 1];
+      }
     }
   }
 }
