@@ -113,17 +113,26 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// n and 1/n for the interior-face count n in 1..6, by selection (no
-// conversion or division instructions).
+// n (exactly) and 1/n (to single precision) for the interior-face count n in
+// 1..6.  A chain of selections between constants was measured to cost ~430
+// cycles per use (an indexed constant-table load); these are a few integer
+// or single-precision instructions.  The double n is assembled from its bits
+// (exponent floor(log2 n), mantissa n shifted into place), so no FP64-pipe
+// conversion is spent on it.  1/n only scales smoother updates and stored
+// Jacobian constants (never a term of a residual), so single precision
+// suffices.
 template <typename T>
-__device__ __forceinline__ T count_value(int n) {
-  return n == 4 ? T(4) : n == 2 ? T(2) : n == 3 ? T(3) : n == 6 ? T(6) : n == 5 ? T(5) : T(1);
+__device__ __forceinline__ T count_value(int n);
+template <>
+__device__ __forceinline__ float count_value<float>(int n) { return (float)n; }
+template <>
+__device__ __forceinline__ double count_value<double>(int n) {
+  const int e = 31 - __clz(n);
+  const unsigned hi = ((unsigned)(1023 + e) << 20) | (((unsigned)n << (20 - e)) & 0xFFFFFu);
+  return __hiloint2double((int)hi, 0);
 }
 template <typename T>
-__device__ __forceinline__ T inv_count(int n) {
-  return n == 4 ? T(0.25) : n == 2 ? T(0.5) : n == 3 ? T(1.0 / 3.0) : n == 6 ? T(1.0 / 6.0)
-         : n == 5 ? T(0.2) : T(1);
-}
+__device__ __forceinline__ T inv_count(int n) { return T(__frcp_rn((float)n)); }
 
 // Programmatic dependent launch: the kernels of a step are launched so that
 // each may be scheduled while its predecessor drains (its blocks trigger the
@@ -323,8 +332,10 @@ __global__ void __launch_bounds__(kBlock) k_coef_restrict(Level<T> L, Coefs<T> K
 //   Ae = A - C G / Dn = (s/h^2)(sum M_f - gamma (sum a_f)^2 / n_c) >= s n_c / h^2,
 //   dphi = (R1 - Ae R2 - C (R3/Dn)) / (1 + Ae B),  dmu = R2 + B dphi,
 //   dp = R3/Dn - (G/Dn) dmu,
-// with R = f - N(u) at the cell.  R3/Dn is formed directly:
-//   R3/Dn = f3/Dn + (sum p_e + gamma (sum a_f mu_e - sa mu_c)) / n_c - p_c.
+// with R = f - N(u) at the cell.  R3 is formed as the residual itself and
+// then scaled by 1/Dn = h^2/n_c (a stored constant that may be inexact: it
+// only scales the update, while an inexact factor applied before the
+// subtraction of n_c p_c would move the smoother's fixed point).
 // The constants Ae, C, G/Dn, 1/Dn and Q (B = P'(phi), cubic_P) come from
 // coef_at; chi_a in the correction form is taken at phi_b + e.
 template <typename T, int DIM, bool CORR>
@@ -348,7 +359,7 @@ __device__ __forceinline__ void cell_update(const Level<T>& L, const Coefs<T>& K
     R2 = ((f2 - muc) - L.e34ih2 * S.phi) + t2 * phic;
     B = (T(0.25) * phic + t) * phic + t2;
   }
-  T R3n = L.cHn[c] * f3 + ((S.p + K.gamma * (S.amu - sa * muc)) * inv_count<T>(S.m) - pc);
+  T R3n = L.cHn[c] * (f3 + L.ih2 * ((S.p - count_value<T>(S.m) * pc) + K.gamma * (S.amu - sa * muc)));
   T Ae = L.cAe[c];
   T dphi = ((R1 - Ae * R2) - L.cC[c] * R3n) * rcp_approx(T(1) + Ae * B);
   T dmu = R2 + B * dphi;

@@ -35,7 +35,7 @@
 namespace chhs_dev {
 
 constexpr int kTileW = 32, kTileH = 16;  // tile interior (even, so restriction stays inside)
-constexpr int kTileThreads = 256;
+constexpr int kTileThreads = 512;
 
 template <bool CORR>
 __host__ __device__ constexpr int tile_nfields() { return CORR ? 9 : 8; }

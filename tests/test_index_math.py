@@ -31,3 +31,13 @@ def test_small_div_sampled_full_range():
     q = rng.integers(0, (1 << 21) // 2048, size=d.size, dtype=np.int64)
     for t in (q * d, q * d + d - 1, np.maximum(q * d - 1, 0)):
         assert np.array_equal(small_div(t, d), t // d)
+
+
+def test_count_value_bits():
+    """count_value<double> assembles n (1 <= n < 2^20) from its bits:
+    exponent floor(log2 n) and n shifted into the 20 high mantissa bits."""
+    import struct
+    for n in list(range(1, 4097)) + [(1 << 20) - 1]:
+        e = n.bit_length() - 1  # 31 - clz(n)
+        hi = ((1023 + e) << 20) | ((n << (20 - e)) & 0xFFFFF)
+        assert struct.unpack("<d", struct.pack("<Q", hi << 32))[0] == float(n)
