@@ -71,6 +71,12 @@ int level_fields(int dim, bool single) {
 constexpr int kTailCellsF64 = 64;
 constexpr int kTailCellsF32 = 1024;
 
+// Double-precision levels with at most this many threads per colour pass
+// (one per cell of the colour) use the split update (k_smooth_split): up to
+// 128 x 128 in 2D, where a pass has at most one warp per sub-partition's
+// worth of groups.
+constexpr int kSplitThreads = 8192;
+
 struct Layout {
   std::vector<Shape> shapes;
   size_t state_off, partial_off, phimm1_off;
@@ -270,11 +276,20 @@ struct Enqueue {
     const Coefs<T> K = coefs<T>(run);
     const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
     const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
+    // small double-precision levels: each cell's update split over three warps
+    const bool split = std::is_same<T, double>::value && !CORR && threads <= kSplitThreads &&
+                       L.ncell != run->ncell();
     for (int it = 0; it < sweeps; ++it)
       for (int colour = 0; colour < 2; ++colour) {
         const int with_rhs = (rhs && it == 0) ? 1 : 0;
         const int kind = L.ncell == run->ncell() ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH;
         launch(run, s, kind, colour_cells(L, colour), [&] {
+          if constexpr (std::is_same<T, double>::value && !CORR) {
+            if (split) {
+              pdl(k_smooth_split<DIM>, (threads + 31) / 32, 96, s, L, K, colour, with_rhs);
+              return;
+            }
+          }
           pdl(k_smooth<T, DIM, CORR>, blocks, kSmoothBlock, s, L, K, colour, with_rhs);
         });
       }

@@ -415,6 +415,160 @@ __global__ void __launch_bounds__(kSmoothBlock) k_smooth(Level<T> L, Coefs<T> K,
   cell_update<T, DIM, CORR>(L, K, c, i, j, k, f1, f2, f3);
 }
 
+// ---------------------------------------------------------------- split update
+//
+// On small double-precision levels a colour pass is one warp's chain of FP64
+// instructions, and each FP64 warp instruction holds its sub-partition's
+// FP64 pipe for ~64 cycles however few lanes are live.  So the update of a
+// cell is split over the three warps of a group (three sub-partitions, three
+// FP64 pipes): warp 0 forms R1 (and the phi row of the FAS right-hand side),
+// warp 1 R3/Dn (pressure row), warp 2 R2, B and 1/(1 + Ae B) (mu row); warps
+// 1 and 2 hand their values over through shared memory and warp 0 finishes
+// the update.  Same formulas as cell_update, plain form only.
+//
+// The face loop of the split update: for every face of cell c, in the order
+// of nb_sums, fn(in, es, fs) with the neighbour es and face-coefficient
+// index fs (both c itself for a missing face).
+template <int DIM, class FN>
+__device__ __forceinline__ void for_faces(const Level<double>& L, int c, int i, int j, int k, FN fn) {
+  const int sy = L.nx, sz = L.nx * L.ny;
+  auto f = [&](bool in, int e, int fe, int dir) { fn(in, in ? e : c, in ? fe : c, dir); };
+  f(i > 0, c - 1, c - 1, 0);
+  f(i + 1 < L.nx, c + 1, c, 0);
+  f(j > 0, c - sy, c - sy, 1);
+  f(j + 1 < L.ny, c + sy, c, 1);
+  if (DIM == 3) {
+    f(k > 0, c - sz, c - sz, 2);
+    f(k + 1 < L.nz, c + sz, c, 2);
+  }
+}
+
+// x: this lane's four exchange slots, stride 32.  bar() synchronises the
+// three warps of the group; every warp of the group calls this the same
+// number of times (act may be false).
+template <int DIM, class BAR>
+__device__ __forceinline__ void cell_update_split(const Level<double>& L, const Coefs<double>& K, int role,
+                                                  bool act, int c, int i, int j, int k, bool rhs, double* x,
+                                                  BAR bar) {
+  const double* af[3] = {L.ax, L.ay, L.az};
+  const double* Mf[3] = {L.Mx, L.My, L.Mz};
+  double R1 = 0.0, phic = 0.0, muc = 0.0, pc = 0.0, Ae = 0.0, cC = 0.0, cGn = 0.0;
+  if (act) {
+    const double sa = L.sa[c];
+    if (role == 0) {
+      double Mp = -0.0;
+      for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
+        const double a0 = af[d][fs], M0 = Mf[d][fs], mue = L.mu[es], pe = L.p[es];
+        const double a = in ? a0 : 0.0, M = in ? M0 : 0.0;
+        Mp += M * mue;
+        Mp += a * pe;
+      });
+      phic = L.phi[c];
+      muc = L.mu[c];
+      pc = L.p[c];
+      Ae = L.cAe[c];
+      cC = L.cC[c];
+      cGn = L.cGn[c];
+      const double sM = L.sM[c];
+      double f1 = L.fphi[c];
+      if (rhs) {
+        double Mp0 = -0.0;
+        for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
+          const double a0 = af[d][fs], M0 = Mf[d][fs], mue = L.mu0[es], pe = L.p0[es];
+          const double a = in ? a0 : 0.0, M = in ? M0 : 0.0;
+          Mp0 += M * mue;
+          Mp0 += a * pe;
+        });
+        f1 += L.phi0[c] - L.sih2 * ((Mp0 - sM * L.mu0[c]) - sa * L.p0[c]);
+        L.fphi[c] = f1;
+      }
+      R1 = (f1 - phic) + L.sih2 * ((Mp - sM * muc) - sa * pc);
+    } else if (role == 1) {
+      double amu = -0.0, sp = -0.0;
+      int m = 0;
+      for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
+        const double a0 = af[d][fs], mue = L.mu[es], pe = L.p[es];
+        const double a = in ? a0 : 0.0;
+        amu += a * mue;
+        sp += in ? pe : -0.0;
+        m += in ? 1 : 0;
+      });
+      const double mm = count_value<double>(m);
+      double f3 = L.fp[c];
+      if (rhs) {
+        double amu0 = -0.0, sp0 = -0.0;
+        for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
+          const double a0 = af[d][fs], mue = L.mu0[es], pe = L.p0[es];
+          const double a = in ? a0 : 0.0;
+          amu0 += a * mue;
+          sp0 += in ? pe : -0.0;
+        });
+        f3 += -L.ih2 * ((sp0 - mm * L.p0[c]) + K.gamma * (amu0 - sa * L.mu0[c]));
+        L.fp[c] = f3;
+      }
+      x[0] = L.cHn[c] * (f3 + L.ih2 * ((sp - mm * L.p[c]) + K.gamma * (amu - sa * L.mu[c])));
+    } else {
+      double sphi = -0.0;
+      for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
+        const double ph = L.phi[es];
+        sphi += in ? ph : -0.0;
+      });
+      const double v = L.phi[c], pm = L.phim[c], Q = L.cQ[c], hp = 0.25 * pm;
+      double f2 = L.fmu[c];
+      if (rhs) {
+        double sphi0 = -0.0;
+        for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
+          const double ph = L.phi0[es];
+          sphi0 += in ? ph : -0.0;
+        });
+        f2 += (L.mu0[c] + L.e34ih2 * sphi0) - cubic_P(L.phi0[c], hp, Q);
+        L.fmu[c] = f2;
+      }
+      const double t = 0.25 * v + hp;
+      const double t2 = t * v + Q;
+      const double R2 = ((f2 - L.mu[c]) - L.e34ih2 * sphi) + t2 * v;
+      const double B = (0.25 * v + t) * v + t2;
+      x[32] = R2;
+      x[64] = B;
+      x[96] = rcp_approx(1.0 + L.cAe[c] * B);
+    }
+  }
+  bar();
+  if (act && role == 0) {
+    const double R3n = x[0], R2 = x[32], B = x[64], rd = x[96];
+    const double dphi = ((R1 - Ae * R2) - cC * R3n) * rd;
+    const double dmu = R2 + B * dphi;
+    const double dp = R3n - cGn * dmu;
+    L.phi[c] = phic + dphi;
+    L.mu[c] = muc + dmu;
+    L.p[c] = pc + dp;
+  }
+}
+
+// Colour pass of a small double-precision level with the split update: one
+// group of three warps (96 threads) per 32 cells of the colour.
+template <int DIM>
+__global__ void __launch_bounds__(96) k_smooth_split(Level<double> L, Coefs<double> K, int colour, int rhs) {
+  pdl_enter();
+  __shared__ double xch[4 * 32];
+  const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hw = (L.nx + 1) >> 1;
+  const int t = blockIdx.x * 32 + lane;
+  int row, k;
+  if (t < (1 << 21)) {
+    row = small_div(t, L.rhw);
+    k = small_div(row, L.rny);
+  } else {
+    row = t / hw;
+    k = row / L.ny;
+  }
+  const int ti = t - row * hw, j = row - k * L.ny;
+  const int i = 2 * ti + ((j + k + colour) & 1);
+  const bool act = k < L.nz && i < L.nx;
+  const int c = act ? i + L.nx * (j + L.ny * k) : 0;
+  cell_update_split<DIM>(L, K, role, act, c, i, j, k, rhs != 0, xch + lane, [] { __syncthreads(); });
+}
+
 // f_c += N_c(R u) on every cell (used when there is no pre-smoothing sweep to
 // carry it).
 template <typename T, int DIM, bool CORR>
@@ -764,21 +918,48 @@ struct Tail {
   int top_rhs;  // complete the FAS right-hand side of the tail's top level first
 };
 
+// Groups of three warps in the tail block for the split update (warp 15 idles).
+constexpr int kTailGroups = kTailThreads / 96;
+
 template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void tail_smooth(const Level<T>& L, const Coefs<T>& K, int colour, bool rhs) {
   const int hw = (L.nx + 1) >> 1;
   const int total = hw * L.ny * L.nz;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int row = small_div(t, L.rhw);
-    const int ti = t - row * hw;
-    const int k = small_div(row, L.rny);
-    const int j = row - k * L.ny;
-    const int i = 2 * ti + ((j + k + colour) & 1);
-    if (i >= L.nx) continue;
-    const int c = i + L.nx * (j + L.ny * k);
-    T f1, f2, f3;
-    cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, rhs, f1, f2, f3);
-    cell_update<T, DIM, CORR>(L, K, c, i, j, k, f1, f2, f3);
+  if constexpr (!CORR && sizeof(T) == 8) {
+    // plain double precision: split update, groups of three warps, named
+    // barrier per group; every group runs the same number of rounds
+    __shared__ double xch[2][kTailGroups][4 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = warp / 3, role = warp - 3 * g;
+    if (g < kTailGroups) {
+      const int rounds = (total + 32 * kTailGroups - 1) / (32 * kTailGroups);
+      for (int r = 0; r < rounds; ++r) {
+        const int t = r * 32 * kTailGroups + g * 32 + lane;
+        const int row = small_div(t, L.rhw);
+        const int ti = t - row * hw;
+        const int k = small_div(row, L.rny);
+        const int j = row - k * L.ny;
+        const int i = 2 * ti + ((j + k + colour) & 1);
+        const bool act = t < total && i < L.nx;
+        const int c = act ? i + L.nx * (j + L.ny * k) : 0;
+        cell_update_split<DIM>(L, K, role, act, c, i, j, k, rhs, &xch[r & 1][g][lane], [g] {
+          asm volatile("bar.sync %0, 96;" ::"r"(g + 1) : "memory");
+        });
+      }
+    }
+  } else {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int row = small_div(t, L.rhw);
+      const int ti = t - row * hw;
+      const int k = small_div(row, L.rny);
+      const int j = row - k * L.ny;
+      const int i = 2 * ti + ((j + k + colour) & 1);
+      if (i >= L.nx) continue;
+      const int c = i + L.nx * (j + L.ny * k);
+      T f1, f2, f3;
+      cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, rhs, f1, f2, f3);
+      cell_update<T, DIM, CORR>(L, K, c, i, j, k, f1, f2, f3);
+    }
   }
   __syncthreads();
 }
