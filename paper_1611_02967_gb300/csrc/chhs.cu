@@ -350,6 +350,12 @@ struct Enqueue {
     const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
     const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
     launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
+      if constexpr (std::is_same<T, double>::value && !CORR) {
+        if (L.ncell <= 2 * kSplitThreads && l > 0) {  // small level: the three rows on three warps
+          pdl(k_residual_restrict_split<DIM>, (int)tiles, 96, s, L, C, K);
+          return;
+        }
+      }
       pdl(k_residual_restrict<T, DIM, CORR>, rblocks, kBlock, s, L, C, K);
     });
     vcycle<T, CORR>(run, s, lev, tail, l + 1);

@@ -641,6 +641,93 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(Level<T> F, Level<
   if (CORR) C.phib[q] = w * v[NV - 1];
 }
 
+// k_residual_restrict for small double-precision levels (plain form): the
+// three warps of a block take the phi, pressure and mu rows of the same
+// 16 x 2 (8 x 2 x 2) tile, so each warp's FP64 chain is a third as long.
+// Each row's coarse values depend on that row only, so the warps need no
+// exchange: warp 0 writes f_phi and phi (phi^0), warp 1 f_p and p (p^0),
+// warp 2 f_mu and mu (mu^0).  Same formulas as eval_N.
+template <int DIM>
+__global__ void __launch_bounds__(96) k_residual_restrict_split(Level<double> F, Level<double> C,
+                                                                Coefs<double> K) {
+  pdl_enter();
+  constexpr int TX = DIM == 3 ? 8 : 16;
+  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+  const int tile = blockIdx.x;
+  const int tiles_x = (F.nx + TX - 1) / TX;
+  const int tiles_y = F.ny >> 1;
+  const int tx = tile % tiles_x;
+  const int rest = tile / tiles_x;
+  const int ty = rest % tiles_y, tz = rest / tiles_y;
+  const int i = tx * TX + (lane % TX);
+  const int j = 2 * ty + ((lane / TX) & 1);
+  const int k = DIM == 3 ? 2 * tz + (lane >> 4) : 0;
+  const bool valid = i < F.nx;
+  const double* af[3] = {F.ax, F.ay, F.az};
+  const double* Mf[3] = {F.Mx, F.My, F.Mz};
+  double r = 0.0, u = 0.0;
+  if (valid) {
+    const int c = i + F.nx * (j + F.ny * k);
+    const double sa = F.sa[c];
+    if (role == 0) {
+      double Mp = -0.0;
+      for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
+        const double a0 = af[d][fs], M0 = Mf[d][fs], mue = F.mu[es], pe = F.p[es];
+        const double a = in ? a0 : 0.0, M = in ? M0 : 0.0;
+        Mp += M * mue;
+        Mp += a * pe;
+      });
+      const double phic = F.phi[c];
+      r = F.fphi[c] - (phic - F.sih2 * ((Mp - F.sM[c] * F.mu[c]) - sa * F.p[c]));
+      u = phic;
+    } else if (role == 1) {
+      double amu = -0.0, sp = -0.0;
+      int m = 0;
+      for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
+        const double a0 = af[d][fs], mue = F.mu[es], pe = F.p[es];
+        const double a = in ? a0 : 0.0;
+        amu += a * mue;
+        sp += in ? pe : -0.0;
+        m += in ? 1 : 0;
+      });
+      const double pc = F.p[c];
+      r = F.fp[c] - (-F.ih2 * ((sp - count_value<double>(m) * pc) + K.gamma * (amu - sa * F.mu[c])));
+      u = pc;
+    } else {
+      double sphi = -0.0;
+      for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
+        const double ph = F.phi[es];
+        sphi += in ? ph : -0.0;
+      });
+      const double muc = F.mu[c];
+      r = F.fmu[c] - ((muc + F.e34ih2 * sphi) - cubic_P(F.phi[c], 0.25 * F.phim[c], F.cQ[c]));
+      u = muc;
+    }
+  }
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  u += __shfl_xor_sync(0xffffffffu, u, 1);
+  r += __shfl_xor_sync(0xffffffffu, r, TX);
+  u += __shfl_xor_sync(0xffffffffu, u, TX);
+  if (DIM == 3) {
+    r += __shfl_xor_sync(0xffffffffu, r, 16);
+    u += __shfl_xor_sync(0xffffffffu, u, 16);
+  }
+  const bool leader = valid && (lane & 1) == 0 && ((lane / TX) & 1) == 0 && (DIM == 2 || lane < 16);
+  if (!leader) return;
+  const double w = DIM == 3 ? 0.125 : 0.25;
+  const int q = (i >> 1) + C.nx * ((j >> 1) + C.ny * (k >> 1));
+  if (role == 0) {
+    C.fphi[q] = w * r;
+    C.phi[q] = C.phi0[q] = w * u;
+  } else if (role == 1) {
+    C.fp[q] = w * r;
+    C.p[q] = C.p0[q] = w * u;
+  } else {
+    C.fmu[q] = w * r;
+    C.mu[q] = C.mu0[q] = w * u;
+  }
+}
+
 // u += P(u_c - u_c^0), P piecewise constant.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
