@@ -160,6 +160,18 @@ chhs_status chhs_energy(chhs_t* run, double* E_out, double* F_out);
  * is nullable.  Meaningful after at least one chhs_step. */
 chhs_status chhs_dissipation(chhs_t* run, double* grad_mu_sq, double* u_sq, double* div_u_max);
 
+/* The velocity of the last accepted step on the face grid (Eq. 2.3,
+ * u = -grad_h p - gamma A_h phi* grad_h mu, with the face average A_h of
+ * Appendix A.1): ux[c] is the x-component on the face between cell c and its
+ * +x neighbour, uy and uz likewise for +y and +z, each an array of N values
+ * in the layout of phi; faces on the domain boundary hold 0 (no flux).  uz is
+ * ignored in 2D (may be NULL) and required in 3D.  Device pointers if
+ * on_device, else host memory owned by the caller.  Blocks until the copy is
+ * done.  Meaningful after at least one chhs_step.  Errors:
+ * CHHS_ERR_INVALID_ARG (null run, ux, uy, or uz in 3D; steps enqueued by
+ * chhs_step_async and not yet waited for), CHHS_ERR_CUDA. */
+chhs_status chhs_velocity(chhs_t* run, double* ux, double* uy, double* uz, int on_device);
+
 /* Copy out phi^m (the latest accepted step). */
 chhs_status chhs_get_phi(chhs_t* run, double* out, int on_device);
 

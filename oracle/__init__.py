@@ -47,7 +47,7 @@ def lib():
         L.oracle_mass.restype = d
         L.oracle_energy.argtypes = [i, _ip, d, d, _dp, _dp, _dp, _dp]
         L.oracle_energy.restype = None
-        L.oracle_velocity.argtypes = [i, _ip, d, d, _dp, _dp, _dp, _dp]
+        L.oracle_velocity.argtypes = [i, _ip, d, d, _dp, _dp, _dp, _dp, _dp]
         L.oracle_velocity.restype = d
         L.oracle_num_levels.argtypes = [i, _ip, i]
         L.oracle_num_levels.restype = i
@@ -150,8 +150,19 @@ def velocity(phis, mu, p, h, gamma):
     phis, mu, p = map(_f64, (phis, mu, p))
     dim, n = _dims(phis.shape)
     div = np.empty_like(phis)
-    u2 = lib().oracle_velocity(dim, n, float(h), float(gamma), _ptr(phis), _ptr(mu), _ptr(p), _ptr(div))
+    u2 = lib().oracle_velocity(dim, n, float(h), float(gamma), _ptr(phis), _ptr(mu), _ptr(p), _ptr(div), None)
     return u2, div
+
+
+def face_velocity(phis, mu, p, h, gamma):
+    """The velocity of Eq. 2.3 on the face grid: array (dim,) + shape whose
+    [a][c] entry is the a-component on the face between cell c and its +a
+    neighbour (0 on boundary faces)."""
+    phis, mu, p = map(_f64, (phis, mu, p))
+    dim, n = _dims(phis.shape)
+    faces = np.zeros((dim,) + phis.shape)
+    lib().oracle_velocity(dim, n, float(h), float(gamma), _ptr(phis), _ptr(mu), _ptr(p), None, _ptr(faces))
+    return faces
 
 
 def num_levels(shape, coarsest=2):

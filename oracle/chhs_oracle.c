@@ -506,13 +506,18 @@ void oracle_energy(int dim, const int* n, double h, double eps, const double* ph
 /*
  * Velocity of Eq. 2.3, u = -grad_h p - gamma A_h phi* grad_h mu, on interior
  * faces (boundary faces carry u.n = 0).  Writes ||u||_2^2 with the face inner
- * product of Appendix A.2 and, if div_out is given, div_h u per cell.
+ * product of Appendix A.2, if div_out is given div_h u per cell, and if
+ * faces_out is given the face values themselves: faces_out[a * N + c] is the
+ * a-component on the face between cell c and its +a neighbour (0 where that
+ * face is a boundary face).
  */
 double oracle_velocity(int dim, const int* n, double h, double gamma,
-                       const double* phis, const double* mu, const double* p, double* div_out) {
+                       const double* phis, const double* mu, const double* p, double* div_out,
+                       double* faces_out) {
     int nx = n[0], ny = n[1], nz = dim == 3 ? n[2] : 1;
     int nc = nx * ny * nz;
     if (div_out) for (int c = 0; c < nc; ++c) div_out[c] = 0.0;
+    if (faces_out) for (int c = 0; c < dim * nc; ++c) faces_out[c] = 0.0;
     ksum_t acc = {0, 0};
     int stride[3] = {1, nx, nx * ny};
     for (int k = 0; k < nz; ++k)
@@ -527,6 +532,7 @@ double oracle_velocity(int dim, const int* n, double h, double gamma,
                     double u = -(p[e] - p[c]) / h - gamma * af * (mu[e] - mu[c]) / h;
                     kadd(&acc, u * u);
                     if (div_out) { div_out[c] += u / h; div_out[e] -= u / h; }
+                    if (faces_out) faces_out[a * nc + c] = u;
                 }
             }
     return (dim == 2 ? h * h : h * h * h) * kval(&acc);

@@ -27,7 +27,7 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_mass", "chhs_energy", "chhs_get_phi", "chhs_get_state", "chhs_set_state",
            "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc", "chhs_dissipation",
            "chhs_server_create", "chhs_server_submit", "chhs_server_wait", "chhs_server_result",
-           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth"]
+           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
@@ -85,6 +85,7 @@ def lib():
             "chhs_server_stats": (i, [_vp, _ip, _ip, _ip, ctypes.POINTER(sz)]),
             "chhs_server_destroy": (None, [_vp]),
             "chhs_profile_smooth": (i, [_vp, i, _dp]),
+            "chhs_velocity": (i, [_vp, _dp, _dp, _dp, i]),
             "chhs_get_phi": (i, [_vp, _vp, i]),
             "chhs_get_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
             "chhs_set_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
@@ -257,6 +258,15 @@ class Run:
         ms = ctypes.c_double(0.0)
         self._check(lib().chhs_profile_smooth(self.handle, int(npasses), ctypes.byref(ms)))
         return ms.value
+
+    def velocity(self):
+        """Face velocities of the last accepted step (Eq. 2.3): array (dim,) +
+        shape, [a][c] on the face between cell c and its +a neighbour."""
+        dim = len(self.shape)
+        u = np.zeros((dim,) + tuple(self.shape))
+        ptr = [u[a].ctypes.data_as(_dp) for a in range(dim)] + [None] * (3 - dim)
+        self._check(lib().chhs_velocity(self.handle, ptr[0], ptr[1], ptr[2], 0))
+        return u
 
     def mass(self):
         m = ctypes.c_double(0.0)

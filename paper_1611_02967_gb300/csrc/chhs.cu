@@ -524,6 +524,14 @@ struct Enqueue {
     return CHHS_OK;
   }
 
+  // Face velocities into out[0..DIM) (device arrays of ncell values).
+  static chhs_status velocity(chhs_t* run, double* const* out) {
+    k_velocity<DIM><<<nblocks(run->ncell()), kBlock, 0, run->stream>>>(run->lev[0], run->gamma, 1.0 / run->h,
+                                                                         out[0], out[1], out[2]);
+    CU(cudaGetLastError());
+    return CHHS_OK;
+  }
+
   static chhs_status energy(chhs_t* run) {
     const int nx = run->n[0], ny = run->n[1], nz = run->n[2];
     const int nb = nblocks(run->ncell());
@@ -899,6 +907,26 @@ chhs_status chhs_dissipation(chhs_t* run, double* grad_mu_sq, double* u_sq, doub
   if (grad_mu_sq) *grad_mu_sq = hd * d[0];
   if (u_sq) *u_sq = hd * d[1];
   if (div_u_max) *div_u_max = d[2];
+  return CHHS_OK;
+}
+
+chhs_status chhs_velocity(chhs_t* run, double* ux, double* uy, double* uz, int on_device) {
+  if (!run || !ux || !uy || (run->dim == 3 && !uz)) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
+  if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
+  run->err.clear();
+  double* dst[3] = {ux, uy, run->dim == 3 ? uz : nullptr};
+  // host outputs are staged in the finest level's R u arrays, which only the
+  // coarse levels use
+  const Level<double>& F = run->lev[0];
+  double* stage[3] = {F.phi0, F.mu0, F.p0};
+  double* out[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < run->dim; ++a) out[a] = on_device ? dst[a] : stage[a];
+  chhs_status s = run->dim == 2 ? Enqueue<2>::velocity(run, out) : Enqueue<3>::velocity(run, out);
+  if (s != CHHS_OK) return s;
+  if (!on_device)
+    for (int a = 0; a < run->dim; ++a)
+      if ((s = copy_out(run, dst[a], stage[a], 0)) != CHHS_OK) return s;
+  CU(cudaStreamSynchronize(run->stream));
   return CHHS_OK;
 }
 

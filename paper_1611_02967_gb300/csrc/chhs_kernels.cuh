@@ -1357,6 +1357,27 @@ __global__ void __launch_bounds__(kBlock) k_dissip_partial(Level<double> L, doub
   }
 }
 
+// The velocity of Eq. 2.3 on the face grid: ux[c] (uy, uz) is the
+// component on the face between cell c and its +x (+y, +z) neighbour, zero on
+// boundary faces; the same face formula as k_dissip_partial.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_velocity(Level<double> L, double gamma, double ih, double* ux,
+                                                     double* uy, double* uz) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.ncell) return;
+  int i, j, k;
+  cell_ijk(c, L.nx, L.ny, i, j, k);
+  const double muc = L.mu[c], pc = L.p[c], psc = L.phis[c];
+  auto face = [&](bool in, int e) {
+    if (!in) return 0.0;
+    const double gmu = (L.mu[e] - muc) * ih;
+    return -(L.p[e] - pc) * ih - gamma * 0.5 * (psc + L.phis[e]) * gmu;
+  };
+  ux[c] = face(i + 1 < L.nx, c + 1);
+  uy[c] = face(j + 1 < L.ny, c + L.nx);
+  if (DIM == 3) uz[c] = face(k + 1 < L.nz, c + L.nx * L.ny);
+}
+
 static __global__ void k_dissip_finish(const double* partials, int nparts, DevState* st) {
   if (threadIdx.x != 0) return;
   double a = 0.0, b = 0.0, m = 0.0;

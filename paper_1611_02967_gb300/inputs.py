@@ -48,6 +48,17 @@ def cosine_bump(n, L):
     return (1.0 - np.cos(4.0 * np.pi * X / L)) * (1.0 - np.cos(2.0 * np.pi * Y / L)) / 2.0 - 1.0
 
 
+def cosine_bump3(n, L):
+    """A 3D analogue of Eq. 5.1 on (0,L)^3 (the paper's test is 2D only):
+    ([1 - cos(4 pi x/L)][1 - cos(2 pi y/L)][1 - cos(2 pi z/L)])/4 - 1 at cell
+    centres, shape (z, y, x); values in [-1, 1], mean -3/4."""
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    return ((1.0 - np.cos(4.0 * np.pi * X / L)) * (1.0 - np.cos(2.0 * np.pi * Y / L))
+            * (1.0 - np.cos(2.0 * np.pi * Z / L)) / 4.0 - 1.0)
+
+
 def bubbles(n, L, eps, seed, count=8, rmin=0.5, rmax=1.0):
     """3D tanh bubbles on a phi = -1 background.
 

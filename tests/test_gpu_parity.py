@@ -243,3 +243,37 @@ def test_profile_smooth_keeps_state():
         for a, b in zip(before, after):
             assert np.array_equal(a, b)
         run.step(1)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape,h,eps,gamma,dt", [((48, 32), 0.05, 0.05, 2.0, 0.01),
+                                                  ((16, 8, 12), 0.1, 0.08, 1.5, 0.005)])
+def test_face_velocity_matches_oracle(shape, h, eps, gamma, dt, precision):
+    """chhs_velocity: the face velocity of Eq. 2.3 from the GPU's own step
+    equals the oracle's face formula on the same fields, its squares sum to
+    the dissipation norm, and the device-output path gives the same bits."""
+    import torch
+    phi0 = inputs.spinodal(shape, 17, mean=0.0, amplitude=0.4)
+    dim = len(shape)
+    with _run(shape, h, eps, gamma, dt, precision) as run:
+        run.set_phi(phi0)
+        run.step(2)
+        phim, phimm1, _, _ = run.get_state()
+        run.step(1)
+        _, _, mu, p = run.get_state()
+        u = run.velocity()
+        ou = oracle.face_velocity(1.5 * phim - 0.5 * phimm1, mu, p, h, gamma)
+        scale = max(1.0, np.max(np.abs(ou)))
+        assert np.max(np.abs(u - ou)) <= 1e-12 * scale
+        _, u2, _ = run.dissipation()
+        assert abs(h ** dim * np.sum(u * u) - u2) <= 1e-12 * max(u2, 1e-300)
+        ud = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
+        s = chhs.lib().chhs_velocity(run.handle, *[ctypes_ptr(ud[a]) for a in range(3)], 1)
+        assert s == chhs.CHHS_OK
+        torch.cuda.synchronize()
+        assert np.array_equal(ud[:dim].cpu().numpy(), u)
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double))

@@ -67,3 +67,42 @@ def test_table1_cauchy_convergence_on_gpu():
         assert abs(rate - printed[n][0]) <= 0.1, (n, rate, printed[n])
     for n in (32, 64, 128, 256, 512):
         assert abs(nv[n] - printed[n][1]) <= 1.5, (n, nv[n], printed[n])
+
+
+def _golden_module(name):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(name, os.path.join(GOLDEN, name + ".py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_3d_cauchy_convergence_on_gpu():
+    """A 3D version of the Table 1 experiment (the paper prints 2D only): the
+    3D analogue of Eq. 5.1 on (0,3.2)^3 with the Table 1 parameters, grids 8^3
+    ... 128^3.  The GPU's Cauchy differences equal the CPU oracle's
+    (tests/golden/e1_3d_oracle.txt) where the oracle can afford them, the
+    rates rise towards the scheme's second order, and mass is conserved
+    (initial mass -3/4 L^3 in closed form)."""
+    tri = _golden_module("make_e1_3d_oracle").trilinear
+    sols, nv = {}, {}
+    mass0 = -0.75 * L ** 3
+    for n in (8, 16, 32, 64, 128):
+        h = L / n
+        s = 0.05 * h
+        steps = int(round(0.8 / s))
+        with chhs.Run((n, n, n), h, 0.2, 2.0, s) as run:
+            run.set_phi(inputs.cosine_bump3(n, L))
+            assert abs(run.mass() - mass0) < 1e-11
+            _, v, r = run.step(steps)
+            assert r <= 1e-10
+            assert abs(run.mass() - mass0) < steps * L ** 3 * 1.1e-10
+            sols[n], nv[n] = run.get_phi(), v / steps
+    err = {n: np.sqrt((L / n) ** 3 * np.sum((sols[n] - tri(sols[n // 2])) ** 2)) for n in (16, 32, 64, 128)}
+    rate = {n: np.log2(err[n // 2] / err[n]) for n in (32, 64, 128)}
+    print("GPU 3D Cauchy:", {n: "%.4e (V %.2f)" % (err[n], nv[n]) for n in err}, "rates", rate)
+    for n_s, e_s, v_s in _read("e1_3d_oracle.txt"):
+        n = int(n_s)
+        assert abs(err[n] - float(e_s)) <= 1e-4 * float(e_s), (n, err[n], e_s)
+    assert rate[32] < rate[64] < rate[128] + 0.05
+    assert abs(rate[128] - 2.0) <= 0.2, rate
