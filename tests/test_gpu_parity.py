@@ -277,3 +277,33 @@ def test_face_velocity_matches_oracle(shape, h, eps, gamma, dt, precision):
 def ctypes_ptr(t):
     import ctypes
     return ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("case", ["spinodal2048", "bubbles256"])
+def test_largest_served_sizes_satisfy_the_scheme(case, precision):
+    """The largest runs the request loop serves (2048^2 and 256^3 cells) are
+    beyond what the oracle can solve in a test, so each GPU step is checked
+    by a property that holds at any size: the oracle's own double-precision
+    residual of Eqs. 2.5-2.7, evaluated on the GPU's (phi, mu, p) with the
+    step's (phi^m, phi^{m-1}), is at the solver's tolerance, and mass is
+    conserved to |Omega| tol."""
+    if case == "spinodal2048":
+        shape, h, eps, gamma, dt = (2048, 2048), 0.025, 0.05, 2.0, 0.005
+        phi0 = inputs.spinodal(shape, 21, mean=-0.1, amplitude=0.05)
+    else:
+        shape, h, eps, gamma, dt = (256, 256, 256), 0.05, 0.04, 2.0, 0.005
+        phi0 = inputs.bubbles(256, 256 * h, eps, 22)
+    prm = oracle.Params(h, eps, gamma, dt)
+    vol = np.prod(shape) * h ** len(shape)
+    with _run(shape, h, eps, gamma, dt, precision) as run:
+        run.set_phi(phi0)
+        for _ in range(2):
+            phim, phimm1, _, _ = run.get_state()
+            m0 = run.mass()
+            s, v, r = run.step(1)
+            assert r <= 1e-10
+            phi, _, mu, p = run.get_state()
+            nrm = oracle.residual(phim, phimm1, phi, mu, p, prm)[3]
+            assert nrm <= 2e-10, (nrm, r)
+            assert abs(run.mass() - m0) <= 1.1e-10 * vol
