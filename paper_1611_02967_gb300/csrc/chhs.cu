@@ -319,7 +319,7 @@ struct Enqueue {
       // the pre-smoothing launch writes the second copy of the state (and the
       // completed right-hand side), the post-smoothing launch reads them and
       // writes the state back: no launch writes what its own tiles read
-      const TileOut<T> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3};
+      const TileOut<T> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3, nullptr, nullptr, nullptr};
       Level<T> Lb = L;
       Lb.phi = L.phi2;
       Lb.mu = L.mu2;
@@ -329,7 +329,12 @@ struct Enqueue {
         Lb.fmu = L.fc2;
         Lb.fp = L.fc3;
       }
-      const TileOut<T> to_state{L.phi, L.mu, L.p, nullptr, nullptr, nullptr};
+      TileOut<T> to_state{L.phi, L.mu, L.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+      if (l == 0 && fused_update(run)) {  // the finished correction goes straight into u
+        to_state.phi64 = run->lev[0].phi;
+        to_state.mu64 = run->lev[0].mu;
+        to_state.p64 = run->lev[0].p;
+      }
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu1, [&] {
         pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
                  np1 + 1, rhs ? 1 : 0, 0, 1, to_copy);
@@ -366,6 +371,10 @@ struct Enqueue {
   }
 
   static bool mixed(const chhs_t* run) { return run->opts.precision == 1; }
+
+  // Mixed form whose finest level is tiled (2D, not the tail): the last tile
+  // launch of a V-cycle performs the update u <- u + e (k_mixed_update otherwise).
+  static bool fused_update(const chhs_t* run) { return mixed(run) && DIM == 2 && run->tail_start > 0; }
 
   // The fused tile kernels serve the 2D single-precision V-cycles.
   template <typename T>
@@ -409,9 +418,10 @@ struct Enqueue {
     if (mixed(run)) {
       vcycle<float, true>(run, s, run->lev32, run->tail32, 0);
       const Level<double>& L = run->lev[0];
-      launch(run, s, CHHS_K_FRAME, 1.0, [&] {
-        pdl(k_mixed_update, nblocks(L.ncell), kBlock, s, L, run->lev32[0]);
-      });
+      if (!fused_update(run))
+        launch(run, s, CHHS_K_FRAME, 1.0, [&] {
+          pdl(k_mixed_update, nblocks(L.ncell), kBlock, s, L, run->lev32[0]);
+        });
     } else {
       vcycle<double, false>(run, s, run->lev, run->tail, 0);
     }

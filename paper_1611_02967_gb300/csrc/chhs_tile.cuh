@@ -78,10 +78,13 @@ __device__ __forceinline__ void local_coef(const T* ps, int s, int SW, int i, in
 }
 
 // Where a tile launch writes its interior: (phi, mu, p) and, with rhs, the
-// completed right-hand side.
+// completed right-hand side.  On the finest level of the mixed form the
+// post-smoothing launch instead adds the finished correction to the
+// double-precision iterate (phi64, mu64, p64 non-null): u <- u + e.
 template <typename T>
 struct TileOut {
   T *phi, *mu, *p, *f1, *f2, *f3;
+  double *phi64, *mu64, *p64;
 };
 
 // Shared-memory views of one tile's fields.
@@ -241,9 +244,15 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
       const int q = small_div(t, rw);
       int j = y0 + q, i = x0 + (t - q * w);
       int s = (i - gx0) + SW * (j - gy0), c = i + nx * j;
-      out.phi[c] = V.phi[s];
-      out.mu[c] = V.mu[s];
-      out.p[c] = V.p[s];
+      if (out.phi64) {
+        out.phi64[c] += (double)V.phi[s];
+        out.mu64[c] += (double)V.mu[s];
+        out.p64[c] += (double)V.p[s];
+      } else {
+        out.phi[c] = V.phi[s];
+        out.mu[c] = V.mu[s];
+        out.p[c] = V.p[s];
+      }
       if (rhs) {
         out.f1[c] = V.f1[s];
         out.f2[c] = V.f2[s];
