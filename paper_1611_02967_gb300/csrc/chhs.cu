@@ -404,11 +404,12 @@ struct Enqueue {
   static void norm(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int mode, int use_cond) {
     const Coefs<double> K = coefs<double>(run);
     const Level<double>& L = run->lev[0];
+    const int nb = (L.ncell + kBlock * kNormCells - 1) / (kBlock * kNormCells);
     launch(run, s, CHHS_K_NORM, L.ncell, [&] {
       if (mixed(run))
-        pdl(k_norm_mixed<DIM>, nblocks(L.ncell), kBlock, s, L, K, run->lev32[0], run->partials, run->st, cond, mode, use_cond);
+        pdl(k_norm_mixed<DIM>, nb, kBlock, s, L, K, run->lev32[0], run->partials, run->st, cond, mode, use_cond);
       else
-        pdl(k_norm<double, DIM>, nblocks(L.ncell), kBlock, s, L, K, run->partials, run->st, cond, mode, use_cond);
+        pdl(k_norm<double, DIM>, nb, kBlock, s, L, K, run->partials, run->st, cond, mode, use_cond);
     });
   }
 

@@ -27,6 +27,7 @@
 namespace chhs_dev {
 
 constexpr int kBlock = 256;        // block size of the plain per-cell kernels
+constexpr int kNormCells = 4;      // cells per thread of the norm kernels (amortises their block sums)
 constexpr int kSmoothBlock = 128;  // block size of the smoother (more, smaller blocks per SM)
 constexpr int kTailThreads = 512;  // one block runs the coarse tail of a V-cycle
 constexpr int kTailMaxLevels = 12;
@@ -816,17 +817,22 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
                                                  cudaGraphConditionalHandle cond, int mode, int use_cond) {
   pdl_enter();
   __shared__ bool last;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[2] = {0.0, 0.0};
-  if (c < L.ncell) {
+  const int base = blockIdx.x * blockDim.x * kNormCells + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kNormCells; ++q) {
+    const int c = base + q * blockDim.x;
+    if (c >= L.ncell) break;
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
     T n1, n2, n3;
     eval_N<T, DIM, false>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
     double r1 = double(L.fphi[c] - n1), r2 = double(L.fmu[c] - n2);
     double r3 = double(K.s) * double(L.fp[c] - n3);
-    acc[0] = r1 * r1 + r2 * r2 + r3 * r3;
-    acc[1] = double(L.p[c]);
+    acc[0] = fma(r1, r1, acc[0]);
+    acc[0] = fma(r2, r2, acc[0]);
+    acc[0] = fma(r3, r3, acc[0]);
+    acc[1] += double(L.p[c]);
   }
   block_sum<2>(acc);
   if (threadIdx.x == 0) {
@@ -885,17 +891,22 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
                                                        cudaGraphConditionalHandle cond, int mode, int use_cond) {
   pdl_enter();
   __shared__ bool last;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[2] = {0.0, 0.0};
-  if (c < L.ncell) {
+  const int base = blockIdx.x * blockDim.x * kNormCells + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kNormCells; ++q) {
+    const int c = base + q * blockDim.x;
+    if (c >= L.ncell) break;
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
     double n1, n2, n3;
     eval_N<double, DIM, false>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
     double r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = L.fp[c] - n3;
     double r3s = K.s * r3;
-    acc[0] = r1 * r1 + r2 * r2 + r3s * r3s;
-    acc[1] = L.p[c];
+    acc[0] = fma(r1, r1, acc[0]);
+    acc[0] = fma(r2, r2, acc[0]);
+    acc[0] = fma(r3s, r3s, acc[0]);
+    acc[1] += L.p[c];
     G.fphi[c] = (float)r1;
     G.fmu[c] = (float)r2;
     G.fp[c] = (float)r3;
