@@ -429,7 +429,16 @@ struct Enqueue {
     norm(run, s, cond, 1, use_cond);
   }
 
+  // The step's set-up: phi*, f, the initial guess and the finest level's
+  // coefficients (frame_setup), then the coarser levels' coefficients
+  // (frame_coefs), which only the V-cycles need: in the step graph they run
+  // beside the initial stopping norm.
   static void frame_head(chhs_t* run, cudaStream_t s) {
+    frame_setup(run, s);
+    frame_coefs(run, s);
+  }
+
+  static void frame_setup(chhs_t* run, cudaStream_t s) {
     const Level<double>& F = run->lev[0];
     const Coefs<double> K = coefs<double>(run);
     const std::vector<Level<double>>& D = run->lev;
@@ -438,6 +447,13 @@ struct Enqueue {
       pdl(k_setup_coef<DIM>, nblocks(F.ncell), kBlock, s, F, run->phimm1, run->eps * run->eps, run->st, K,
           nd > 1 ? D[1] : D[0], nd > 1 ? 1 : 0);
     });
+  }
+
+  static void frame_coefs(chhs_t* run, cudaStream_t s) {
+    const Level<double>& F = run->lev[0];
+    const Coefs<double> K = coefs<double>(run);
+    const std::vector<Level<double>>& D = run->lev;
+    const int nd = (int)D.size();
     for (int l = 1; l < nd; ++l)
       launch(run, s, CHHS_K_FRAME, 1.0, [&] {
         pdl(k_coef_restrict<double, DIM>, nblocks(D[l].ncell), kBlock, s, D[l], K, l + 1 < nd ? D[l + 1] : D[l],
@@ -468,13 +484,22 @@ struct Enqueue {
   static chhs_status build_graph(chhs_t* run) {
     chhs_status ps = mixed(run) ? prepare_tail<float, true>(run, run->tail32) : prepare_tail<double, false>(run, run->tail);
     if (ps != CHHS_OK) return ps;
-    cudaStream_t cs = nullptr, cs2 = nullptr;
+    cudaStream_t cs = nullptr, cs2 = nullptr, cs3 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&cs3, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
     int n_frame = 0, n_v = 0;
     CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     run->counter = &n_frame;
-    frame_head(run, cs);
+    frame_setup(run, cs);
+    // the coarser levels' coefficients on a side branch, beside the initial norm
+    CU(cudaEventRecord(fork, cs));
+    CU(cudaStreamWaitEvent(cs3, fork, 0));
+    frame_coefs(run, cs3);
+    CU(cudaEventRecord(join, cs3));
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -483,6 +508,7 @@ struct Enqueue {
     cudaGraphConditionalHandle cond;
     CU(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
     norm(run, cs, cond, 0, 1);
+    CU(cudaStreamWaitEvent(cs, join, 0));
     CU(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps));
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.conditional.handle = cond;
@@ -501,6 +527,9 @@ struct Enqueue {
     run->counter = nullptr;
     CU(cudaStreamEndCapture(cs, &run->graph));
     CU(cudaGraphInstantiate(&run->exec, run->graph, 0));
+    CU(cudaEventDestroy(fork));
+    CU(cudaEventDestroy(join));
+    CU(cudaStreamDestroy(cs3));
     CU(cudaStreamDestroy(cs2));
     CU(cudaStreamDestroy(cs));
     run->launches_per_v = n_v;
