@@ -121,7 +121,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // (exponent floor(log2 n), mantissa n shifted into place), so no FP64-pipe
 // conversion is spent on it.  1/n only scales smoother updates and stored
 // Jacobian constants (never a term of a residual), so single precision
-// suffices.
+// suffices (the hardware reciprocal approximation in single-precision code).
 template <typename T>
 __device__ __forceinline__ T count_value(int n);
 template <>
@@ -134,6 +134,8 @@ __device__ __forceinline__ double count_value<double>(int n) {
 }
 template <typename T>
 __device__ __forceinline__ T inv_count(int n) { return T(__frcp_rn((float)n)); }
+template <>
+__device__ __forceinline__ float inv_count<float>(int n) { return rcp_approx((float)n); }
 
 // Programmatic dependent launch: the kernels of a step are launched so that
 // each may be scheduled while its predecessor drains (its blocks trigger the
