@@ -644,6 +644,53 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(Level<T> F, Level<
   if (CORR) C.phib[q] = w * v[NV - 1];
 }
 
+// One row of the plain form's N at cell c, on the fields (phi, mu, p):
+// role 0 gives N1, role 1 N3, role 2 N2 (eval_N's formulas, one row each, so
+// three warps can share a cell's work).  u returns the row's own unknown at c
+// (phi, p or mu).  f_row gives the matching right-hand side.
+template <int DIM>
+__device__ __forceinline__ double n_row(const Level<double>& F, const Coefs<double>& K, int role,
+                                        const double* phi, const double* mu, const double* p, int c, int i,
+                                        int j, int k, double& u) {
+  const double* af[3] = {F.ax, F.ay, F.az};
+  const double* Mf[3] = {F.Mx, F.My, F.Mz};
+  const double sa = F.sa[c];
+  if (role == 0) {
+    double Mp = -0.0;
+    for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
+      const double a0 = af[d][fs], M0 = Mf[d][fs], mue = mu[es], pe = p[es];
+      const double a = in ? a0 : 0.0, M = in ? M0 : 0.0;
+      Mp += M * mue;
+      Mp += a * pe;
+    });
+    u = phi[c];
+    return u - F.sih2 * ((Mp - F.sM[c] * mu[c]) - sa * p[c]);
+  }
+  if (role == 1) {
+    double amu = -0.0, sp = -0.0;
+    int m = 0;
+    for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
+      const double a0 = af[d][fs], mue = mu[es], pe = p[es];
+      const double a = in ? a0 : 0.0;
+      amu += a * mue;
+      sp += in ? pe : -0.0;
+      m += in ? 1 : 0;
+    });
+    u = p[c];
+    return -F.ih2 * ((sp - count_value<double>(m) * u) + K.gamma * (amu - sa * mu[c]));
+  }
+  double sphi = -0.0;
+  for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
+    const double ph = phi[es];
+    sphi += in ? ph : -0.0;
+  });
+  u = mu[c];
+  return (u + F.e34ih2 * sphi) - cubic_P(phi[c], 0.25 * F.phim[c], F.cQ[c]);
+}
+__device__ __forceinline__ double* f_row(const Level<double>& F, int role) {
+  return role == 0 ? F.fphi : role == 1 ? F.fp : F.fmu;
+}
+
 // k_residual_restrict for small double-precision levels (plain form): the
 // three warps of a block take the phi, pressure and mu rows of the same
 // 16 x 2 (8 x 2 x 2) tile, so each warp's FP64 chain is a third as long.
@@ -666,46 +713,11 @@ __global__ void __launch_bounds__(96) k_residual_restrict_split(Level<double> F,
   const int j = 2 * ty + ((lane / TX) & 1);
   const int k = DIM == 3 ? 2 * tz + (lane >> 4) : 0;
   const bool valid = i < F.nx;
-  const double* af[3] = {F.ax, F.ay, F.az};
-  const double* Mf[3] = {F.Mx, F.My, F.Mz};
   double r = 0.0, u = 0.0;
   if (valid) {
     const int c = i + F.nx * (j + F.ny * k);
-    const double sa = F.sa[c];
-    if (role == 0) {
-      double Mp = -0.0;
-      for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
-        const double a0 = af[d][fs], M0 = Mf[d][fs], mue = F.mu[es], pe = F.p[es];
-        const double a = in ? a0 : 0.0, M = in ? M0 : 0.0;
-        Mp += M * mue;
-        Mp += a * pe;
-      });
-      const double phic = F.phi[c];
-      r = F.fphi[c] - (phic - F.sih2 * ((Mp - F.sM[c] * F.mu[c]) - sa * F.p[c]));
-      u = phic;
-    } else if (role == 1) {
-      double amu = -0.0, sp = -0.0;
-      int m = 0;
-      for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
-        const double a0 = af[d][fs], mue = F.mu[es], pe = F.p[es];
-        const double a = in ? a0 : 0.0;
-        amu += a * mue;
-        sp += in ? pe : -0.0;
-        m += in ? 1 : 0;
-      });
-      const double pc = F.p[c];
-      r = F.fp[c] - (-F.ih2 * ((sp - count_value<double>(m) * pc) + K.gamma * (amu - sa * F.mu[c])));
-      u = pc;
-    } else {
-      double sphi = -0.0;
-      for_faces<DIM>(F, c, i, j, k, [&](bool in, int es, int fs, int d) {
-        const double ph = F.phi[es];
-        sphi += in ? ph : -0.0;
-      });
-      const double muc = F.mu[c];
-      r = F.fmu[c] - ((muc + F.e34ih2 * sphi) - cubic_P(F.phi[c], 0.25 * F.phim[c], F.cQ[c]));
-      u = muc;
-    }
+    const double n = n_row<DIM>(F, K, role, F.phi, F.mu, F.p, c, i, j, k, u);
+    r = f_row(F, role)[c] - n;
   }
   r += __shfl_xor_sync(0xffffffffu, r, 1);
   u += __shfl_xor_sync(0xffffffffu, u, 1);
@@ -1066,11 +1078,24 @@ __device__ __forceinline__ void tail_smooth(const Level<T>& L, const Coefs<T>& K
 
 template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void tail_rhs(const Level<T>& L, const Coefs<T>& K) {
-  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
-    int i, j, k;
-    cell_ijk_small(c, L, i, j, k);
-    T f1, f2, f3;
-    cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, true, f1, f2, f3);
+  if constexpr (!CORR && sizeof(T) == 8) {
+    // plain double precision: the three rows of N(R u) on three warps of a group
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = warp / 3, role = warp - 3 * g;
+    if (g < kTailGroups)
+      for (int c = g * 32 + lane; c < L.ncell; c += 32 * kTailGroups) {
+        int i, j, k;
+        cell_ijk_small(c, L, i, j, k);
+        double u;
+        f_row(L, role)[c] += n_row<DIM>(L, K, role, L.phi0, L.mu0, L.p0, c, i, j, k, u);
+      }
+  } else {
+    for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+      int i, j, k;
+      cell_ijk_small(c, L, i, j, k);
+      T f1, f2, f3;
+      cell_rhs<T, DIM, CORR>(L, K, c, i, j, k, true, f1, f2, f3);
+    }
   }
   __syncthreads();
 }
@@ -1082,6 +1107,50 @@ __device__ __forceinline__ void tail_rhs(const Level<T>& L, const Coefs<T>& K) {
 template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void tail_restrict(const Level<T>& F, const Level<T>& C, const Coefs<T>& K) {
   constexpr int NCH = DIM == 3 ? 8 : 4;
+  if constexpr (!CORR && sizeof(T) == 8) {
+    // plain double precision: the phi, pressure and mu rows on the three warps
+    // of a group (n_row), each writing its own coarse values
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = warp / 3, role = warp - 3 * g;
+    if (g < kTailGroups) {
+      const double w = DIM == 3 ? 0.125 : 0.25;
+      const int total = C.ncell * NCH;
+      const int rounds = (total + 32 * kTailGroups - 1) / (32 * kTailGroups);
+      for (int r = 0; r < rounds; ++r) {
+        const int t = r * 32 * kTailGroups + g * 32 + lane;
+        const bool act = t < total;
+        const int q = t / NCH, d = t % NCH;
+        double rr = 0.0, u = 0.0;
+        if (act) {
+          int I, J, KK;
+          cell_ijk_small(q, C, I, J, KK);
+          const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * KK + (d >> 2);
+          const int c = i + F.nx * (j + F.ny * k);
+          const double n = n_row<DIM>(F, K, role, F.phi, F.mu, F.p, c, i, j, k, u);
+          rr = f_row(F, role)[c] - n;
+        }
+#pragma unroll
+        for (int o = 1; o < NCH; o <<= 1) {
+          rr += __shfl_xor_sync(0xffffffffu, rr, o);
+          u += __shfl_xor_sync(0xffffffffu, u, o);
+        }
+        if (act && d == 0) {
+          if (role == 0) {
+            C.fphi[q] = w * rr;
+            C.phi[q] = C.phi0[q] = w * u;
+          } else if (role == 1) {
+            C.fp[q] = w * rr;
+            C.p[q] = C.p0[q] = w * u;
+          } else {
+            C.fmu[q] = w * rr;
+            C.mu[q] = C.mu0[q] = w * u;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
   constexpr int NV = CORR ? 7 : 6;
   const T w = DIM == 3 ? T(0.125) : T(0.25);
   const int total = C.ncell * NCH;
@@ -1157,22 +1226,36 @@ __device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>
   const int nw = min((L.ncell + 31) >> 5, (int)(blockDim.x >> 5));
   float acc0 = -1.f, prev = 0.f;
   for (int it = 0; it <= kCoarsestMaxSweeps; ++it) {
-    if ((int)threadIdx.x < nw * 32) {
-      T acc = T(0);
-      for (int c = threadIdx.x; c < L.ncell; c += nw * 32) {
-        int i, j, k;
-        cell_ijk_small(c, L, i, j, k);
-        T n1, n2, n3;
-        eval_N<T, DIM, CORR>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
-        T r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = K.s * (L.fp[c] - n3);
-        acc += r1 * r1 + r2 * r2 + r3 * r3;
-      }
-      float a = warp_sum((float)acc);
-      if ((threadIdx.x & 31) == 0) sh_part[threadIdx.x >> 5] = a;
+    // every warp writes its partial (zero without cells)
+    T acc = T(0);
+    if constexpr (!CORR && sizeof(T) == 8) {
+      // plain double precision: the three rows on the three warps of a group
+      const int warp = threadIdx.x >> 5, g = warp / 3, role = warp - 3 * g;
+      if (g < kTailGroups)
+        for (int c = g * 32 + (threadIdx.x & 31); c < L.ncell; c += 32 * kTailGroups) {
+          int i, j, k;
+          cell_ijk_small(c, L, i, j, k);
+          double u;
+          double r = f_row(L, role)[c] - n_row<DIM>(L, K, role, L.phi, L.mu, L.p, c, i, j, k, u);
+          if (role == 1) r *= K.s;
+          acc += r * r;
+        }
+    } else {
+      if ((int)threadIdx.x < nw * 32)
+        for (int c = threadIdx.x; c < L.ncell; c += nw * 32) {
+          int i, j, k;
+          cell_ijk_small(c, L, i, j, k);
+          T n1, n2, n3;
+          eval_N<T, DIM, CORR>(L, K, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
+          T r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = K.s * (L.fp[c] - n3);
+          acc += r1 * r1 + r2 * r2 + r3 * r3;
+        }
     }
+    const float a = warp_sum((float)acc);
+    if ((threadIdx.x & 31) == 0) sh_part[threadIdx.x >> 5] = a;
     __syncthreads();
     float tot = 0.f;
-    for (int w = 0; w < nw; ++w) tot += sh_part[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh_part[w];
     if (acc0 < 0.f) acc0 = tot;
     if (!(tot > kCoarsestTarget2 * acc0) || tot < 1e-37f) break;
     if (it >= 8 && tot >= prev) break;
