@@ -896,9 +896,26 @@ __global__ void __launch_bounds__(kBlock) k_coef_restrict_f32(Level<double> F, L
     restrict_coef_at<float, double, DIM>(F, Gn, i, j, k, pm, ps);
 }
 
+// Double to single precision with integer instructions, truncating toward
+// zero: a conversion instruction costs as much as an FP64 FMA on this GPU
+// (measured), these are a handful of integer operations.  For the values it
+// sees (residuals and phi, far inside the single-precision range) the result
+// is x with its mantissa cut to 24 bits (relative error below 2^-23);
+// magnitudes under the smallest normal single give 0 and ones beyond its
+// range give infinity.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned bits = e <= 0 ? sign : e >= 255 ? (sign | 0x7F800000u) : (sign | ((unsigned)e << 23) | mant);
+  return __uint_as_float(bits);
+}
+
 // The stopping norm of the double-precision iterate, as k_norm, and the
-// right-hand side of the next inner solve: f32 = r rounded, e = 0,
-// phi_b = phi rounded.
+// right-hand side of the next inner solve: f32 = r cut to single precision,
+// e = 0, phi_b = phi cut to single precision.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<double> K, Level<float> G,
                                                        double* partials, DevState* st,
@@ -921,13 +938,13 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
     acc[0] = fma(r2, r2, acc[0]);
     acc[0] = fma(r3s, r3s, acc[0]);
     acc[1] += L.p[c];
-    G.fphi[c] = (float)r1;
-    G.fmu[c] = (float)r2;
-    G.fp[c] = (float)r3;
+    G.fphi[c] = f64_to_f32_rz(r1);
+    G.fmu[c] = f64_to_f32_rz(r2);
+    G.fp[c] = f64_to_f32_rz(r3);
     G.phi[c] = 0.f;
     G.mu[c] = 0.f;
     G.p[c] = 0.f;
-    G.phib[c] = (float)L.phi[c];
+    G.phib[c] = f64_to_f32_rz(L.phi[c]);
   }
   block_sum<2>(acc);
   if (threadIdx.x == 0) {

@@ -41,3 +41,31 @@ def test_count_value_bits():
         e = n.bit_length() - 1  # 31 - clz(n)
         hi = ((1023 + e) << 20) | ((n << (20 - e)) & 0xFFFFF)
         assert struct.unpack("<d", struct.pack("<Q", hi << 32))[0] == float(n)
+
+
+def test_f64_to_f32_rz_bits():
+    """f64_to_f32_rz (the mixed form's residual hand-over) cuts the mantissa
+    of a double to 24 bits with integer operations: the same as truncating
+    toward zero in single precision for normal values, 0 below the smallest
+    normal single.  Emulated bit for bit."""
+    import struct
+
+    def emu(x):
+        b = struct.unpack("<Q", struct.pack("<d", x))[0]
+        hi, lo = b >> 32, b & 0xFFFFFFFF
+        sign = hi & 0x80000000
+        e = ((hi >> 20) & 0x7FF) - 1023 + 127
+        mant = ((hi & 0xFFFFF) << 3) | (lo >> 29)
+        bits = sign if e <= 0 else (sign | 0x7F800000) if e >= 255 else (sign | (e << 23) | mant)
+        return struct.unpack("<f", struct.pack("<I", bits))[0]
+
+    rng = np.random.default_rng(11)
+    xs = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000), [0.0, -0.0, 1.0, -2.5]])
+    for x in xs:
+        y = emu(float(x))
+        f = np.float32(x)  # round to nearest
+        # truncation: |y| <= |x|, same sign, and within one single-precision ulp of x
+        assert abs(y) <= abs(x) and (y == 0 or np.sign(y) == np.sign(x))
+        assert abs(x - y) <= abs(x) * 2.0 ** -23
+        assert abs(float(f) - y) <= abs(x) * 2.0 ** -23
+    assert emu(1e-40) == 0.0 and emu(3.0) == 3.0
