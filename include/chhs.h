@@ -137,12 +137,12 @@ chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_o
 /* The double-precision smoother on the finest level, alone: npasses colour
  * passes back to back (alternating colours, after one untimed pass) between
  * two CUDA events on the handle's stream; *ms_per_pass = their average
- * duration.  The finest level's (phi, mu, p) are copied to a temporary device
- * buffer first and restored afterwards, so the run's state is unchanged
- * bitwise.  Blocks until done.  Errors: CHHS_ERR_INVALID_ARG (null pointer,
- * npasses < 1, steps enqueued by chhs_step_async and not yet waited for),
- * CHHS_ERR_OOM (no room for the copy), CHHS_ERR_CUDA.  For profiling; it has
- * no counterpart in the paper. */
+ * duration.  The finest level's (phi, mu, p) are copied aside inside the
+ * handle's workspace first and restored afterwards, so the run's state is
+ * unchanged bitwise; nothing is allocated.  Blocks until done.  Errors:
+ * CHHS_ERR_INVALID_ARG (null pointer, npasses < 1, steps enqueued by
+ * chhs_step_async and not yet waited for), CHHS_ERR_CUDA.  For profiling; it
+ * has no counterpart in the paper. */
 chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass);
 
 /* Discrete mass (phi^m, 1) = h^d sum phi^m (Section 4, mass conservation). */

@@ -484,13 +484,34 @@ struct Enqueue {
   static chhs_status build_graph(chhs_t* run) {
     chhs_status ps = mixed(run) ? prepare_tail<float, true>(run, run->tail32) : prepare_tail<double, false>(run, run->tail);
     if (ps != CHHS_OK) return ps;
-    cudaStream_t cs = nullptr, cs2 = nullptr, cs3 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    CU(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
-    CU(cudaStreamCreateWithFlags(&cs3, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    // capture streams and fork/join events, released on every return path (a
+    // capture that an error interrupted is ended and its graph dropped first)
+    struct CaptureRes {
+      cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~CaptureRes() {
+        for (int q : {1, 0}) {
+          cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+          if (s[q] && cudaStreamIsCapturing(s[q], &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s[q], &g);
+            if (q == 0 && g) cudaGraphDestroy(g);  // the body graph belongs to the step graph
+          }
+        }
+        for (cudaEvent_t ev : e)
+          if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t st : s)
+          if (st) cudaStreamDestroy(st);
+        cudaGetLastError();
+      }
+    } res;
+    CU(cudaStreamCreateWithFlags(&res.s[0], cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&res.s[1], cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&res.s[2], cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&res.e[0], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&res.e[1], cudaEventDisableTiming));
+    cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2];
+    cudaEvent_t fork = res.e[0], join = res.e[1];
     int n_frame = 0, n_v = 0;
     CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     run->counter = &n_frame;
@@ -527,11 +548,6 @@ struct Enqueue {
     run->counter = nullptr;
     CU(cudaStreamEndCapture(cs, &run->graph));
     CU(cudaGraphInstantiate(&run->exec, run->graph, 0));
-    CU(cudaEventDestroy(fork));
-    CU(cudaEventDestroy(join));
-    CU(cudaStreamDestroy(cs3));
-    CU(cudaStreamDestroy(cs2));
-    CU(cudaStreamDestroy(cs));
     run->launches_per_v = n_v;
     run->launches_per_step = n_frame;
     return CHHS_OK;
@@ -870,43 +886,41 @@ chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass) {
   if (!run || npasses < 1 || !ms_per_pass) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   run->err.clear();
-  cudaEvent_t a, b;
-  CU(cudaEventCreate(&a));
-  CU(cudaEventCreate(&b));
+  struct Events {  // destroyed on every return path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CU(cudaEventCreate(&ev.a));
+  CU(cudaEventCreate(&ev.b));
   const Level<double>& L = run->lev[0];
   const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
   const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
   const Coefs<double> K{run->dt, run->gamma, 0.75 * run->eps * run->eps};
-  // the passes overwrite (phi, mu, p) of the finest level: keep a copy and put it back
+  // the passes overwrite (phi, mu, p) of the finest level: keep a copy in the
+  // finest level's R u arrays (only the coarse levels use theirs) and put it back
   const size_t bytes = sizeof(double) * (size_t)L.ncell;
-  double* keep = nullptr;
-  if (cudaMalloc(&keep, 3 * bytes) != cudaSuccess) {
-    cudaGetLastError();
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return fail(run, CHHS_ERR_OOM, "cudaMalloc failed");
-  }
-  CU(cudaMemcpyAsync(keep, L.phi, bytes, cudaMemcpyDeviceToDevice, run->stream));
-  CU(cudaMemcpyAsync(keep + L.ncell, L.mu, bytes, cudaMemcpyDeviceToDevice, run->stream));
-  CU(cudaMemcpyAsync(keep + 2 * (size_t)L.ncell, L.p, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.phi0, L.phi, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.mu0, L.mu, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.p0, L.p, bytes, cudaMemcpyDeviceToDevice, run->stream));
   // one untimed pass, then npasses timed ones back to back
   for (int k = 0; k <= npasses; ++k) {
-    if (k == 1) CU(cudaEventRecord(a, run->stream));
+    if (k == 1) CU(cudaEventRecord(ev.a, run->stream));
     if (run->dim == 2)
       pdl(k_smooth<double, 2, false>, blocks, kSmoothBlock, run->stream, L, K, k & 1, 0);
     else
       pdl(k_smooth<double, 3, false>, blocks, kSmoothBlock, run->stream, L, K, k & 1, 0);
   }
-  CU(cudaEventRecord(b, run->stream));
-  CU(cudaMemcpyAsync(L.phi, keep, bytes, cudaMemcpyDeviceToDevice, run->stream));
-  CU(cudaMemcpyAsync(L.mu, keep + L.ncell, bytes, cudaMemcpyDeviceToDevice, run->stream));
-  CU(cudaMemcpyAsync(L.p, keep + 2 * (size_t)L.ncell, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(ev.b, run->stream));
+  CU(cudaMemcpyAsync(L.phi, L.phi0, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.mu, L.mu0, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.p, L.p0, bytes, cudaMemcpyDeviceToDevice, run->stream));
   CU(cudaStreamSynchronize(run->stream));
-  cudaFree(keep);
   float ms = 0.f;
-  CU(cudaEventElapsedTime(&ms, a, b));
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
   *ms_per_pass = ms / npasses;
   return CHHS_OK;
 }
