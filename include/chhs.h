@@ -72,7 +72,16 @@ size_t chhs_workspace_bytes(int dim, const int n[3], const chhs_opts* opts);
  * step dt > 0 (Section 2).  Every n[a] must be >= 2.  opts NULL means the
  * defaults.  cuda_stream (a cudaStream_t, NULL = a stream the handle creates)
  * orders all of the handle's device work.  Allocates the hierarchy with
- * cudaMalloc.  The state starts at phi^0 = phi^{-1} = 0 until chhs_set_phi. */
+ * cudaMalloc.  The state starts at phi^0 = phi^{-1} = 0 until chhs_set_phi.
+ * The grid is coarsened by 2 while every extent stays even and at least
+ * opts->coarsest; the coarsest level is solved by one thread block, so a
+ * grid whose coarsest level stays large (odd extents such as 65 x 65 give a
+ * single level of 4,225 cells; the limit is about 1,000 cells in double
+ * precision, 2,000 in the mixed form) is rejected with CHHS_ERR_INVALID_ARG,
+ * as are opts with sweep counts too large for the mixed form's tiles.
+ * Errors: CHHS_ERR_INVALID_ARG (dim not 2 or 3, an extent < 2, h, eps or dt
+ * <= 0, gamma < 0, invalid opts, the cases above), CHHS_ERR_OOM,
+ * CHHS_ERR_CUDA. */
 chhs_status chhs_create(int dim, const int n[3], double h, double eps, double gamma, double dt,
                         const chhs_opts* opts, void* cuda_stream, chhs_t** out);
 

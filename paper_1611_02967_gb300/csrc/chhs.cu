@@ -389,12 +389,27 @@ struct Enqueue {
 
   // Opt the tail kernel in to the shared memory its levels need.
   template <typename T, bool CORR>
+  // A grid that does not coarsen far enough leaves a coarsest level too large
+  // for the one-block tail, and very long sweeps make the tiles' halos too
+  // large: both are rejected as invalid arguments before any launch.
   static chhs_status prepare_tail(chhs_t* run, const Tail<T>& tail) {
+    int dev = 0, optin = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto fits = [&](const void* fn, size_t dyn) {
+      cudaFuncAttributes fa;
+      return cudaFuncGetAttributes(&fa, fn) == cudaSuccess && dyn + fa.sharedSizeBytes <= (size_t)optin;
+    };
     const size_t smem = tail_bytes<T, CORR>(tail);
+    if (!fits(reinterpret_cast<const void*>(k_tail<T, DIM, CORR>), smem))
+      return fail(run, CHHS_ERR_INVALID_ARG,
+                  "the grid does not coarsen to a coarsest level small enough for the one-block solve");
     CU(cudaFuncSetAttribute(k_tail<T, DIM, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if constexpr (use_tiles<T>()) {
       const int halo = 2 * std::max(run->opts.nu1, run->opts.nu2) + 1;
       const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T));
+      if (!fits(reinterpret_cast<const void*>(k_tile<T, CORR>), tb))
+        return fail(run, CHHS_ERR_INVALID_ARG, "nu1/nu2 too large for the single-precision tiles");
       CU(cudaFuncSetAttribute(k_tile<T, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb));
     }
     return CHHS_OK;

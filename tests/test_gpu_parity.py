@@ -176,6 +176,15 @@ def test_invalid_arguments_rejected():
         chhs.Run((1, 16), 0.1, 0.05, 1.0, 0.01)
     with pytest.raises(chhs.ChhsError):
         chhs.Run((16, 16), 0.1, 0.05, -1.0, 0.01)
+    # odd extents leave one level of 4225 cells: too large for the one-block coarsest solve
+    for precision in PRECISIONS:
+        with pytest.raises(chhs.ChhsError) as e:
+            chhs.Run((65, 65), 0.1, 0.05, 1.0, 0.01, opts=chhs.default_opts(precision=precision))
+        assert e.value.status == chhs.CHHS_ERR_INVALID_ARG
+    # sweeps too long for the single-precision tiles' halos
+    with pytest.raises(chhs.ChhsError) as e:
+        chhs.Run((64, 64), 0.1, 0.05, 1.0, 0.01, opts=chhs.default_opts(precision=1, nu1=40))
+    assert e.value.status == chhs.CHHS_ERR_INVALID_ARG
     assert chhs.workspace_bytes((512, 512)) > 11 * 512 * 512 * 8
 
 
