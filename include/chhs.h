@@ -154,6 +154,30 @@ chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_o
  * has no counterpart in the paper. */
 chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass);
 
+/* Launch shapes of one handle (see chhs_autotune). */
+typedef struct {
+  int tail_cells;     /* levels with at most this many cells run in the one-block tail */
+  int split_threads;  /* double-precision levels with at most this many cells per colour
+                         use the three-warp split update (0: never) */
+  int tile_threads;   /* threads per tile in the 2D mixed form */
+  double ms_per_step; /* the chosen setting's time per step in the trials */
+} chhs_tuning;
+
+/* Autotuner of the handle's launch shapes: tries candidate settings (where
+ * the one-block tail starts; in double precision, up to which level size the
+ * split update is used; in the 2D mixed form, the tile block size), times
+ * trial_steps steps of the handle's own problem from its current state with
+ * each, keeps the fastest and rebuilds the step graph with it.  The state is
+ * restored after every trial and at the end, so the run continues exactly
+ * where it was.  Candidates that fail (shared memory too small, a trial that
+ * does not converge) are skipped.  Allocates a temporary copy of the state
+ * (4 N doubles).  Blocks until done; out (nullable) receives the chosen
+ * setting.  Errors: CHHS_ERR_INVALID_ARG (null run, trial_steps < 1, steps
+ * enqueued by chhs_step_async and not yet waited for), CHHS_ERR_OOM,
+ * CHHS_ERR_CUDA.  The paper has no counterpart (launch shapes are a property
+ * of this implementation). */
+chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out);
+
 /* Discrete mass (phi^m, 1) = h^d sum phi^m (Section 4, mass conservation). */
 chhs_status chhs_mass(chhs_t* run, double* mass_out);
 

@@ -27,7 +27,8 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_mass", "chhs_energy", "chhs_get_phi", "chhs_get_state", "chhs_set_state",
            "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc", "chhs_dissipation",
            "chhs_server_create", "chhs_server_submit", "chhs_server_wait", "chhs_server_result",
-           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity"]
+           "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity",
+           "chhs_autotune"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
@@ -42,6 +43,12 @@ class chhs_request(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("eps", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("phi0", ctypes.c_void_p), ("phi_prev", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    """chhs_tuning (include/chhs.h)."""
+    _fields_ = [("tail_cells", ctypes.c_int), ("split_threads", ctypes.c_int), ("tile_threads", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double)]
 
 
 class ChhsError(RuntimeError):
@@ -86,6 +93,7 @@ def lib():
             "chhs_server_destroy": (None, [_vp]),
             "chhs_profile_smooth": (i, [_vp, i, _dp]),
             "chhs_velocity": (i, [_vp, _dp, _dp, _dp, i]),
+            "chhs_autotune": (i, [_vp, i, ctypes.c_void_p]),
             "chhs_get_phi": (i, [_vp, _vp, i]),
             "chhs_get_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
             "chhs_set_state": (i, [_vp, _vp, _vp, _vp, _vp, i]),
@@ -267,6 +275,14 @@ class Run:
         ptr = [u[a].ctypes.data_as(_dp) for a in range(dim)] + [None] * (3 - dim)
         self._check(lib().chhs_velocity(self.handle, ptr[0], ptr[1], ptr[2], 0))
         return u
+
+    def autotune(self, trial_steps=3):
+        """chhs_autotune: pick this run's launch shapes by timing its own steps
+        (the state is left as it was).  Returns the chosen setting."""
+        t = Tuning()
+        self._check(lib().chhs_autotune(self.handle, int(trial_steps), ctypes.byref(t)))
+        return dict(tail_cells=t.tail_cells, split_threads=t.split_threads, tile_threads=t.tile_threads,
+                    ms_per_step=t.ms_per_step)
 
     def mass(self):
         m = ctypes.c_double(0.0)

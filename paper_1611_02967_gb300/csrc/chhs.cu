@@ -168,6 +168,11 @@ struct chhs {
   std::vector<Level<double>> lev;   // double precision: all levels, or the finest only when mixed
   std::vector<Level<float>> lev32;  // single-precision correction hierarchy (mixed precision)
   int tail_start = 0;               // first level run by the one-block tail kernel
+  // launch shapes (defaults above; chhs_autotune may change them): levels of at
+  // most tail_cells cells go to the tail, double-precision levels of at most
+  // split_threads threads per colour pass use the split update, tiles run
+  // tile_threads threads
+  int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kTileThreads;
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
@@ -277,7 +282,7 @@ struct Enqueue {
     const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
     const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
     // small double-precision levels: each cell's update split over three warps
-    const bool split = std::is_same<T, double>::value && !CORR && threads <= kSplitThreads &&
+    const bool split = std::is_same<T, double>::value && !CORR && threads <= run->split_threads &&
                        L.ncell != run->ncell();
     for (int it = 0; it < sweeps; ++it)
       for (int colour = 0; colour < 2; ++colour) {
@@ -336,12 +341,12 @@ struct Enqueue {
         to_state.p64 = run->lev[0].p;
       }
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu1, [&] {
-        pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
+        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
                  np1 + 1, rhs ? 1 : 0, 0, 1, to_copy);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu2, [&] {
-        pdl_grid(k_tile<T, CORR>, grid, kTileThreads, tile_smem_bytes(np2, nf, sizeof(T)), s, Lb, C, K, np2, np2,
+        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T)), s, Lb, C, K, np2, np2,
                  0, 1, 0, to_state);
       });
       return;
@@ -356,7 +361,7 @@ struct Enqueue {
     const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
     launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
       if constexpr (std::is_same<T, double>::value && !CORR) {
-        if (L.ncell <= 2 * kSplitThreads && l > 0) {  // small level: the three rows on three warps
+        if (L.ncell <= 2 * run->split_threads && l > 0) {  // small level: the three rows on three warps
           pdl(k_residual_restrict_split<DIM>, (int)tiles, 96, s, L, C, K);
           return;
         }
@@ -400,17 +405,27 @@ struct Enqueue {
       cudaFuncAttributes fa;
       return cudaFuncGetAttributes(&fa, fn) == cudaSuccess && dyn + fa.sharedSizeBytes <= (size_t)optin;
     };
+    // the opt-in is per kernel and process-wide: only ever raise it, so that no
+    // handle lowers it below what another handle's graph launches need
+    auto raise_to = [&](const void* fn, size_t dyn) -> cudaError_t {
+      cudaFuncAttributes fa;
+      cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+      if (e != cudaSuccess || (size_t)fa.maxDynamicSharedSizeBytes >= dyn) return e;
+      return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    };
     const size_t smem = tail_bytes<T, CORR>(tail);
-    if (!fits(reinterpret_cast<const void*>(k_tail<T, DIM, CORR>), smem))
+    const void* ktail = reinterpret_cast<const void*>(k_tail<T, DIM, CORR>);
+    if (!fits(ktail, smem))
       return fail(run, CHHS_ERR_INVALID_ARG,
                   "the grid does not coarsen to a coarsest level small enough for the one-block solve");
-    CU(cudaFuncSetAttribute(k_tail<T, DIM, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CU(raise_to(ktail, smem));
     if constexpr (use_tiles<T>()) {
       const int halo = 2 * std::max(run->opts.nu1, run->opts.nu2) + 1;
       const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T));
-      if (!fits(reinterpret_cast<const void*>(k_tile<T, CORR>), tb))
+      const void* ktile = reinterpret_cast<const void*>(k_tile<T, CORR>);
+      if (!fits(ktile, tb))
         return fail(run, CHHS_ERR_INVALID_ARG, "nu1/nu2 too large for the single-precision tiles");
-      CU(cudaFuncSetAttribute(k_tile<T, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb));
+      CU(raise_to(ktile, tb));
     }
     return CHHS_OK;
   }
@@ -673,6 +688,20 @@ void fill_tail(Tail<T>& tail, const std::vector<Level<T>>& lev, int start, const
   tail.top_rhs = start > 0 ? 1 : 0;
 }
 
+// The first level of the one-block tail: the coarsest, and every level above
+// it with at most tail_cells cells (up to kTailMaxLevels levels).
+void place_tail(chhs_t* run) {
+  const Layout& Lo = run->layout;
+  const int nl = (int)Lo.shapes.size();
+  auto cells = [&](int l) { return Lo.shapes[l].n[0] * Lo.shapes[l].n[1] * Lo.shapes[l].n[2]; };
+  run->tail_start = nl - 1;
+  while (run->tail_start > 0 && cells(run->tail_start - 1) <= run->tail_cells &&
+         nl - (run->tail_start - 1) <= kTailMaxLevels)
+    --run->tail_start;
+  fill_tail(run->tail, run->lev, run->tail_start, run->opts);
+  fill_tail(run->tail32, run->lev32, run->tail_start, run->opts);
+}
+
 chhs_status setup_handle(chhs_t* run) {
   const Layout& Lo = run->layout;
   run->st = reinterpret_cast<DevState*>(run->arena + Lo.state_off);
@@ -682,15 +711,8 @@ chhs_status setup_handle(chhs_t* run) {
     run->lev.push_back(make_level<double>(run, Lo.shapes[l], l, run->arena + Lo.level_off[l], false));
   for (size_t l = 0; l < Lo.level32_off.size(); ++l)
     run->lev32.push_back(make_level<float>(run, Lo.shapes[l], (int)l, run->arena + Lo.level32_off[l], true));
-  const int nl = (int)Lo.shapes.size();
-  const int tail_cells = run->opts.precision == 1 ? kTailCellsF32 : kTailCellsF64;
-  run->tail_start = nl - 1;
-  while (run->tail_start > 0 && Lo.shapes[run->tail_start - 1].n[0] * Lo.shapes[run->tail_start - 1].n[1] *
-                                        Lo.shapes[run->tail_start - 1].n[2] <= tail_cells &&
-         nl - (run->tail_start - 1) <= kTailMaxLevels)
-    --run->tail_start;
-  fill_tail(run->tail, run->lev, run->tail_start, run->opts);
-  fill_tail(run->tail32, run->lev32, run->tail_start, run->opts);
+  run->tail_cells = run->opts.precision == 1 ? kTailCellsF32 : kTailCellsF64;
+  place_tail(run);
   CU(cudaMemsetAsync(run->arena, 0, Lo.total, run->stream));
   CU(cudaMallocHost(&run->host_st, sizeof(DevState)));
   memset(run->host_st, 0, sizeof(DevState));
@@ -937,6 +959,101 @@ chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass) {
   float ms = 0.f;
   CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
   *ms_per_pass = ms / npasses;
+  return CHHS_OK;
+}
+
+chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
+  if (!run || trial_steps < 1) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
+  if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
+  run->err.clear();
+  struct Cand {
+    int tail_cells, split_threads, tile_threads;
+  };
+  std::vector<Cand> cands;
+  const bool mixed = run->opts.precision == 1;
+  if (!mixed) {
+    const int tails[2] = {64, run->dim == 2 ? 256 : 512};
+    for (int tc : tails)
+      for (int sp : {0, 8192, 32768}) cands.push_back({tc, sp, run->tile_threads});
+  } else if (run->dim == 2) {
+    for (int tc : {256, 1024, 2048})
+      for (int tt : {256, 512}) cands.push_back({tc, run->split_threads, tt});
+  } else {
+    for (int tc : {64, 512}) cands.push_back({tc, run->split_threads, run->tile_threads});
+  }
+  // the run's state (phi^m, phi^{m-1}, mu, p), restored before every trial and at the end
+  const size_t nc = (size_t)run->ncell(), bytes = sizeof(double) * nc;
+  double* keep = nullptr;
+  if (cudaMalloc(&keep, 4 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(run, CHHS_ERR_OOM, "no room for the state copy");
+  }
+  struct Free {
+    double* p;
+    ~Free() { cudaFree(p); }
+  } free_keep{keep};
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CU(cudaEventCreate(&ev.a));
+  CU(cudaEventCreate(&ev.b));
+  const Level<double>& F = run->lev[0];
+  double* state[4] = {F.phim, run->phimm1, F.mu, F.p};
+  for (int q = 0; q < 4; ++q)
+    CU(cudaMemcpyAsync(keep + q * nc, state[q], bytes, cudaMemcpyDeviceToDevice, run->stream));
+  auto restore = [&]() -> chhs_status {
+    for (int q = 0; q < 4; ++q)
+      CU(cudaMemcpyAsync(state[q], keep + q * nc, bytes, cudaMemcpyDeviceToDevice, run->stream));
+    return CHHS_OK;
+  };
+  auto apply = [&](const Cand& c) -> chhs_status {
+    CU(cudaStreamSynchronize(run->stream));
+    if (run->exec) cudaGraphExecDestroy(run->exec);
+    if (run->graph) cudaGraphDestroy(run->graph);
+    run->exec = nullptr;
+    run->graph = nullptr;
+    run->tail_cells = c.tail_cells;
+    run->split_threads = c.split_threads;
+    run->tile_threads = c.tile_threads;
+    place_tail(run);
+    return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
+  };
+  const Cand orig{run->tail_cells, run->split_threads, run->tile_threads};
+  Cand best = orig;
+  float best_ms = -1.f;
+  chhs_status s;
+  for (const Cand& c : cands) {
+    if (apply(c) != CHHS_OK) continue;  // e.g. a tail too large for shared memory
+    if ((s = restore()) != CHHS_OK) return s;
+    if (chhs_step(run, 1, nullptr, nullptr) != CHHS_OK) continue;  // warm-up
+    if ((s = restore()) != CHHS_OK) return s;
+    CU(cudaEventRecord(ev.a, run->stream));
+    const chhs_status sa = chhs_step_async(run, trial_steps);
+    CU(cudaEventRecord(ev.b, run->stream));
+    if (chhs_wait(run, nullptr, nullptr) != CHHS_OK || sa != CHHS_OK) continue;
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  run->err.clear();
+  if ((s = apply(best)) != CHHS_OK) {
+    if (apply(orig) != CHHS_OK) return fail(run, CHHS_ERR_CUDA, "could not rebuild the step graph");
+  }
+  if ((s = restore()) != CHHS_OK) return s;
+  CU(cudaStreamSynchronize(run->stream));
+  if (out) {
+    out->tail_cells = run->tail_cells;
+    out->split_threads = run->split_threads;
+    out->tile_threads = run->tile_threads;
+    out->ms_per_step = best_ms < 0.f ? -1.0 : (double)best_ms / trial_steps;
+  }
   return CHHS_OK;
 }
 

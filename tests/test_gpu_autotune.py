@@ -1,0 +1,34 @@
+"""chhs_autotune: the launch-shape autotuner leaves the run's state exactly as
+it was, picks one of its candidates, and the tuned handle's next step still
+matches the oracle within the form's tolerance."""
+import numpy as np
+import pytest
+
+from paper_1611_02967_gb300 import chhs, inputs
+from test_gpu_parity import PHI_TOL, _check_step
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape", [(128, 128), (16, 16, 16)])
+def test_autotune_keeps_state_and_steps_match_oracle(shape, precision):
+    h, eps, gamma, dt = 0.05, 0.05, 2.0, 0.01
+    phi0 = inputs.spinodal(shape, 41, mean=0.0, amplitude=0.4)
+    with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=precision)) as run:
+        run.set_phi(phi0)
+        run.step(2)
+        before = run.get_state()
+        t = run.autotune(2)
+        after = run.get_state()
+        for a, b in zip(before, after):
+            assert np.array_equal(a, b)
+        assert t["ms_per_step"] > 0
+        if precision == 0:
+            assert t["tail_cells"] in (64, 256, 512) and t["split_threads"] in (0, 8192, 32768)
+        elif len(shape) == 2:
+            assert t["tail_cells"] in (256, 1024, 2048) and t["tile_threads"] in (256, 512)
+        else:
+            assert t["tail_cells"] in (64, 512)
+        for _ in range(2):
+            _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
