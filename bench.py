@@ -5,6 +5,9 @@ A benchmark step is one time step of the 512 x 512 spinodal workload (2D,
 (0,12.8)^2, eps 0.05, gamma 1, dt 0.005, seeded noise of amplitude 0.05
 about mean 0): one full FAS solve of Eqs. 2.5-2.7 to the 1e-10 stopping norm,
 run through the C ABI.  A cell-step is one cell advanced one time step.
+Before each timed region the handle's launch shapes are picked by
+chhs_autotune on its own problem (untimed, like the warm-up; the state is
+restored) and reported under "tuning".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -326,9 +329,10 @@ def bubbles_leg(stream, flush, steps=10, warmup=3):
             run.step(warmup)
             state = run.get_state()
         run.set_state(*state)
+        tune = run.autotune(2)
         ms, v, r = time_steps(run, steps, stream, flush)
         out[key] = {"value": 128 ** 3 * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-                    "vcycles_per_step": v / steps, "final_resid": r}
+                    "vcycles_per_step": v / steps, "final_resid": r, "tuning": tune}
         run.close()
     return out
 
@@ -373,13 +377,14 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     run = chhs.Run(shape, w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream)
     run.set_phi(w["phi0"])
-    per_v, per_step = run.launch_counts()
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
-    # warm-up (untimed)
+    # warm-up and launch-shape autotuning (both untimed; the tuner restores the state)
     run.step(args.warmup)
+    tuning = {"f64": run.autotune(3)}
+    per_v, per_step = run.launch_counts()
     state0 = run.get_state()  # the e2e leg below replays the same K steps
     # timed region: K steps, L2 flushed before each, device time by events
     barrier(world)
@@ -441,6 +446,7 @@ def run_ours(args):
                      opts=chhs.default_opts(precision=1))
     run32.set_state(*state0)
     run32.step(args.warmup)
+    tuning["mixed"] = run32.autotune(3)
     run32.set_state(*state0)
     barrier(world)
     torch.cuda.synchronize()
@@ -480,6 +486,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config(world), "vcycles_per_step": vtot / args.steps, "final_resid": resid,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "mixed": mixed, "served": served, "batched": batched, "bubbles128": bubbles,
+                "tuning": tuning,
                 "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
