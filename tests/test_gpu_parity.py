@@ -316,3 +316,17 @@ def test_largest_served_sizes_satisfy_the_scheme(case, precision):
             nrm = oracle.residual(phim, phimm1, phi, mu, p, prm)[3]
             assert nrm <= 2e-10, (nrm, r)
             assert abs(run.mass() - m0) <= 1.1e-10 * vol
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("eps,gamma", [(0.02, 0.5), (0.02, 4.0), (0.08, 4.0)])
+def test_served_parameter_extremes_match_oracle(eps, gamma, precision):
+    """Corners of the served parameter range (eps 0.02-0.08, gamma 0.5-4,
+    h 0.025, dt 0.005) on a 256^2 spinodal: every GPU step equals the oracle's
+    converged step within the form's tolerance."""
+    shape, h, dt = (256, 256), 0.025, 0.005
+    phi0 = inputs.spinodal(shape, 61, mean=-0.1, amplitude=0.05)
+    with _run(shape, h, eps, gamma, dt, precision) as run:
+        run.set_phi(phi0)
+        for _ in range(2):
+            _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
