@@ -330,3 +330,18 @@ def test_served_parameter_extremes_match_oracle(eps, gamma, precision):
         run.set_phi(phi0)
         for _ in range(2):
             _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_served_3d_extreme_matches_oracle(precision):
+    """The 3D end of the served range (h 0.05, eps 0.02, gamma 4) on 64^3
+    bubbles: each GPU step equals the oracle's within the form's tolerance.
+    The interfaces are under-resolved here (eps/h = 0.4), and the RMS stop at
+    1e-10 leaves max|dphi| = 1.2e-9 in double precision; as for any such
+    case, the parity run stops the GPU at 1e-11 rather than loosen the bound."""
+    n, h, eps, gamma, dt = 64, 0.05, 0.02, 4.0, 0.005
+    phi0 = inputs.bubbles(n, n * h, eps, 62, count=4, rmin=0.4, rmax=0.8)
+    with _run((n, n, n), h, eps, gamma, dt, precision, tol=1e-11) as run:
+        run.set_phi(phi0)
+        for _ in range(2):
+            _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
