@@ -270,28 +270,46 @@ def time_steps(run, steps, stream, flush):
     return sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), vtot, resid
 
 
-SERVED_DESC = ("served sample: 40 2D spinodal runs, n in {128, 256, 512}^2 (h 0.025), 10-60 steps, "
-               "eps U(0.02,0.08), gamma U(0.5,4), dt 0.005, mixed precision, Poisson arrivals at about "
-               "0.8 of the measured mixed-form capacity, seed 5; 4 GiB pool, 12 active slots, 5 steps per slice")
+SERVED_DESC = ("served sample of the serving configuration: 60 runs, half 2D (n in {128, 256, 512, 1024, "
+               "2048}^2, h 0.025, seeded spinodal) and half 3D (n in {64, 128, 256}^3, h 0.05, 4 tanh bubbles "
+               "up to 128^3, seeded spinodal at 256^3), 10-50 steps (the configuration's 10-500 shortened so the "
+               "sample ends in about half a minute), eps U(0.02,0.08), gamma U(0.5,4), dt 0.005, mixed precision, "
+               "Poisson arrivals at about 0.8 of the measured mixed-form capacity, seed 5; 48 GiB pool, 12 "
+               "active slots, 5 steps per slice")
 
 
-def served_leg(capacity_cell_steps_per_s, seed=5, nruns=40):
+def served_leg(capacity_cell_steps_per_s, seed=5, nruns=60):
     """Continuous batching through chhs_server_*: returns latency percentiles
-    and throughput of a seeded Poisson stream of runs."""
+    and throughput of a seeded Poisson stream of runs drawn from the serving
+    configuration's size and parameter ranges."""
     import numpy as np
 
     from paper_1611_02967_gb300 import chhs, inputs
-    u = inputs.uniform01(seed, nruns * 6, stream=11).reshape(nruns, 6)
-    sizes = np.array([128, 256, 512])[np.minimum((u[:, 0] * 3).astype(int), 2)]
-    steps = 10 + (u[:, 1] * 51).astype(int)
+    u = inputs.uniform01(seed, nruns * 7, stream=11).reshape(nruns, 7)
+    three_d = u[:, 5] < 0.5
+    n2 = np.array([128, 256, 512, 1024, 2048])[np.minimum((u[:, 0] * 5).astype(int), 4)]
+    n3 = np.array([64, 128, 256])[np.minimum((u[:, 0] * 3).astype(int), 2)]
+    sizes = np.where(three_d, n3, n2)
+    steps = 10 + (u[:, 1] * 41).astype(int)
     eps = 0.02 + 0.06 * u[:, 2]
     gamma = 0.5 + 3.5 * u[:, 3]
-    work = sizes.astype(float) ** 2 * steps
+    cells = np.where(three_d, sizes.astype(float) ** 3, sizes.astype(float) ** 2)
+    work = cells * steps
     rate = 0.8 * capacity_cell_steps_per_s / work.mean()        # runs per second
     gaps = -np.log(1.0 - u[:, 4]) / rate                         # exponential inter-arrival times
-    phis = [inputs.spinodal((int(n), int(n)), seed * 1000 + k, mean=0.0) for k, n in enumerate(sizes)]
-    lat, vsum = [], 0
-    with chhs.Server(pool_bytes=4 << 30, max_active=12, steps_per_slice=5) as sv:
+    shapes, hs, phis = [], [], []
+    for k in range(nruns):
+        n = int(sizes[k])
+        if three_d[k]:
+            shapes.append((n, n, n))
+            hs.append(0.05)
+            phis.append(inputs.bubbles(n, n * 0.05, eps[k], seed * 1000 + k, count=4) if n <= 128
+                        else inputs.spinodal((n, n, n), seed * 1000 + k, mean=0.0))
+        else:
+            shapes.append((n, n))
+            hs.append(0.025)
+            phis.append(inputs.spinodal((n, n), seed * 1000 + k, mean=0.0))
+    with chhs.Server(pool_bytes=48 << 30, max_active=12, steps_per_slice=5) as sv:
         t0 = time.perf_counter()
         t_next = t0
         ids = []
@@ -299,8 +317,7 @@ def served_leg(capacity_cell_steps_per_s, seed=5, nruns=40):
             t_next += gaps[k]
             while time.perf_counter() < t_next:
                 time.sleep(0.0002)
-            n = int(sizes[k])
-            ids.append(sv.submit((n, n), 0.025, eps[k], gamma[k], 0.005, int(steps[k]), phis[k], precision=1))
+            ids.append(sv.submit(shapes[k], hs[k], eps[k], gamma[k], 0.005, int(steps[k]), phis[k], precision=1))
         for rid in ids:
             sv.wait(rid, 600.0)
         res = [sv.result(rid, with_phi=False) for rid in ids]
