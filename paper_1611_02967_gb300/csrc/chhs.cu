@@ -56,12 +56,12 @@ std::vector<Shape> level_shapes(int dim, const int n[3], int coarsest) {
 }
 
 // Per-level fields: phi mu p fphi fmu fp phim phis phi0 mu0 p0, ax ay Mx My,
-// sM sa, cAe cC cGn cHn cQ (+ az Mz in 3D), in single precision also phi_b,
+// sM sa, cAe cC cGn cHn cQ cH (+ az Mz in 3D), in single precision also phi_b,
 // and in 2D single precision (the tiled levels) a second (phi, mu, p) and the
 // completed right-hand side.
 constexpr int kBaseFields = 11;
 int level_fields(int dim, bool single) {
-  return kBaseFields + (dim == 3 ? 13 : 11) + (single ? 1 + (dim == 2 ? 6 : 0) : 0);
+  return kBaseFields + (dim == 3 ? 14 : 12) + (single ? 1 + (dim == 2 ? 6 : 0) : 0);
 }
 
 // Levels with at most this many cells run inside the one-block tail kernel.
@@ -645,7 +645,7 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   size_t nc = (size_t)sh.n[0] * sh.n[1] * sh.n[2];
   size_t stride = align_up(sizeof(T) * nc);
   const int nf = level_fields(run->dim, single);
-  T* f[kBaseFields + 20];
+  T* f[kBaseFields + 21];
   for (int q = 0; q < nf; ++q) f[q] = reinterpret_cast<T*>(base + q * stride);
   const double hl = run->h * double(1 << l);
   Level<T> L;
@@ -655,8 +655,8 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
   L.phi0 = f[8]; L.mu0 = f[9]; L.p0 = f[10];
   L.ax = f[11]; L.ay = f[12]; L.Mx = f[13]; L.My = f[14];
   L.sM = f[15]; L.sa = f[16];
-  L.cAe = f[17]; L.cC = f[18]; L.cGn = f[19]; L.cHn = f[20]; L.cQ = f[21];
-  int q = 22;
+  L.cAe = f[17]; L.cC = f[18]; L.cGn = f[19]; L.cHn = f[20]; L.cQ = f[21]; L.cH = f[22];
+  int q = 23;
   L.az = run->dim == 3 ? f[q++] : nullptr;
   L.Mz = run->dim == 3 ? f[q++] : nullptr;
   L.phib = single ? f[q++] : nullptr;

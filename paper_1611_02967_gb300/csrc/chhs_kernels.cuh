@@ -46,7 +46,7 @@ struct Level {
   // cell's interior faces, and the smoother's per-cell constants (coef_at).
   T *ax, *ay, *az, *Mx, *My, *Mz;
   T *sM, *sa;
-  T *cAe, *cC, *cGn, *cHn, *cQ;
+  T *cAe, *cC, *cGn, *cHn, *cQ, *cH;
   int nx, ny, nz;  // nz == 1 in 2D
   int ncell;
   float rnx, rny, rhw;  // 1/nx, 1/ny, 1/ceil(nx/2) in single precision (small_div)
@@ -237,7 +237,7 @@ __device__ __forceinline__ void eval_N(const Level<T>& L, const Coefs<T>& K, con
   if (CORR)
     n2 = muc - chi_term<T, CORR>(L, c, phic, L.phim[c]) + L.e34ih2 * (S.phi - mm * phic);
   else
-    n2 = (muc + L.e34ih2 * S.phi) - cubic_P(phic, T(0.25) * L.phim[c], L.cQ[c]);
+    n2 = (muc + L.e34ih2 * S.phi) - cubic_P(phic, L.cH[c], L.cQ[c]);
   n3 = -L.ih2 * ((S.p - mm * pc) + K.gamma * (S.amu - sa * muc));
 }
 
@@ -246,7 +246,7 @@ __device__ __forceinline__ void eval_N(const Level<T>& L, const Coefs<T>& K, con
 // +x/+y/+z faces, sM = sum M_f and sa = sum a_f over the interior faces, and
 // the smoother's constants (cell_update)
 //   Ae = (s/h^2)(sM - gamma sa^2 / n_c),  C = s sa / h^2,  G/Dn = gamma sa / n_c,
-//   1/Dn = h^2 / n_c,  Q = pm^2/4 + (3/4) eps^2 n_c / h^2.
+//   1/Dn = h^2 / n_c,  Q = pm^2/4 + (3/4) eps^2 n_c / h^2,  and pm/4.
 // ps(e) returns phi* at cell e; pmc is phi^m at c.
 template <typename T, int DIM, class PS>
 __device__ __forceinline__ void coef_at(const Level<T>& L, const Coefs<T>& K, int c, int i, int j, int k,
@@ -285,6 +285,7 @@ __device__ __forceinline__ void coef_at(const Level<T>& L, const Coefs<T>& K, in
   L.cGn[c] = K.gamma * suma * im;
   L.cHn[c] = L.h2 * im;
   L.cQ[c] = T(0.25) * pmc * pmc + L.e34ih2 * count_value<T>(m);
+  L.cH[c] = T(0.25) * pmc;
 }
 
 // phi^m and phi* of the 2^d-cell block whose corner is (i, j, k), restricted
@@ -346,13 +347,13 @@ __device__ __forceinline__ void cell_update(const Level<T>& L, const Coefs<T>& K
                                             int k, T f1, T f2, T f3) {
   Nb<T> S;
   nb_sums<T, DIM>(L, L.phi, L.mu, L.p, c, i, j, k, S);
-  T phic = L.phi[c], muc = L.mu[c], pc = L.p[c], pm = L.phim[c];
+  T phic = L.phi[c], muc = L.mu[c], pc = L.p[c];
   T sM = L.sM[c], sa = L.sa[c], Q = L.cQ[c];
-  T hp = T(0.25) * pm;
+  T hp = L.cH[c];
   T R1 = (f1 - phic) + L.sih2 * ((S.Mp - sM * muc) - sa * pc);
   T R2, B;
   if (CORR) {
-    R2 = f2 - muc + chi_term<T, CORR>(L, c, phic, pm) - L.e34ih2 * (S.phi - count_value<T>(S.m) * phic);
+    R2 = f2 - muc + chi_term<T, CORR>(L, c, phic, L.phim[c]) - L.e34ih2 * (S.phi - count_value<T>(S.m) * phic);
     const T w = L.phib[c] + phic;
     B = (T(0.75) * w + (hp + hp)) * w + Q;
   } else {
@@ -516,7 +517,7 @@ __device__ __forceinline__ void cell_update_split(const Level<double>& L, const 
         const double ph = L.phi[es];
         sphi += in ? ph : -0.0;
       });
-      const double v = L.phi[c], pm = L.phim[c], Q = L.cQ[c], hp = 0.25 * pm;
+      const double v = L.phi[c], Q = L.cQ[c], hp = L.cH[c];
       double f2 = L.fmu[c];
       if (rhs) {
         double sphi0 = -0.0;
@@ -685,7 +686,7 @@ __device__ __forceinline__ double n_row(const Level<double>& F, const Coefs<doub
     sphi += in ? ph : -0.0;
   });
   u = mu[c];
-  return (u + F.e34ih2 * sphi) - cubic_P(phi[c], 0.25 * F.phim[c], F.cQ[c]);
+  return (u + F.e34ih2 * sphi) - cubic_P(phi[c], F.cH[c], F.cQ[c]);
 }
 __device__ __forceinline__ double* f_row(const Level<double>& F, int role) {
   return role == 0 ? F.fphi : role == 1 ? F.fp : F.fmu;
@@ -1288,7 +1289,7 @@ __device__ __forceinline__ void coarsest_solve(const Level<T>& L, const Coefs<T>
 // on every level, the state and right-hand sides (phi, mu, p, f, R u, phi_b)
 // only on the tail's top level; the levels below are computed in place.
 template <int DIM, bool CORR>
-__host__ __device__ constexpr int tail_fields() { return 21 + (DIM == 3 ? 2 : 0) + (CORR ? 1 : 0); }
+__host__ __device__ constexpr int tail_fields() { return 22 + (DIM == 3 ? 2 : 0) + (CORR ? 1 : 0); }
 
 __host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -1315,7 +1316,7 @@ __device__ __forceinline__ Level<T> tail_level(const Tail<T>& tl, int l, unsigne
   L.phim = carve(); L.phi0 = carve(); L.mu0 = carve(); L.p0 = carve();
   L.ax = carve(); L.ay = carve(); L.Mx = carve(); L.My = carve();
   L.sM = carve(); L.sa = carve();
-  L.cAe = carve(); L.cC = carve(); L.cGn = carve(); L.cHn = carve(); L.cQ = carve();
+  L.cAe = carve(); L.cC = carve(); L.cGn = carve(); L.cHn = carve(); L.cQ = carve(); L.cH = carve();
   if (DIM == 3) { L.az = carve(); L.Mz = carve(); }
   if (CORR) L.phib = carve();
   L.phis = nullptr;
@@ -1333,14 +1334,14 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(Tail<T> tl, Coefs<T> K
     const Level<T>& G = tl.lev[l];
     const Level<T> S = tail_level<T, DIM, CORR>(tl, l, tail_smem);
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
-      T v[14];
+      T v[15];
       v[0] = G.phim[c]; v[1] = G.ax[c]; v[2] = G.ay[c]; v[3] = G.Mx[c]; v[4] = G.My[c];
       v[5] = G.sM[c]; v[6] = G.sa[c]; v[7] = G.cAe[c]; v[8] = G.cC[c]; v[9] = G.cGn[c];
-      v[10] = G.cHn[c]; v[11] = G.cQ[c];
+      v[10] = G.cHn[c]; v[11] = G.cQ[c]; v[14] = G.cH[c];
       if (DIM == 3) { v[12] = G.az[c]; v[13] = G.Mz[c]; }
       S.phim[c] = v[0]; S.ax[c] = v[1]; S.ay[c] = v[2]; S.Mx[c] = v[3]; S.My[c] = v[4];
       S.sM[c] = v[5]; S.sa[c] = v[6]; S.cAe[c] = v[7]; S.cC[c] = v[8]; S.cGn[c] = v[9];
-      S.cHn[c] = v[10]; S.cQ[c] = v[11];
+      S.cHn[c] = v[10]; S.cQ[c] = v[11]; S.cH[c] = v[14];
       if (DIM == 3) { S.az[c] = v[12]; S.Mz[c] = v[13]; }
       if (l == 0) {
         T u[10];
