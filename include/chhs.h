@@ -124,15 +124,19 @@ chhs_status chhs_launch_counts(const chhs_t* run, int* per_vcycle, int* per_step
 /* Kernel kinds reported by chhs_profile_step. */
 enum {
     CHHS_K_SMOOTH = 0,      /* one colour pass of the nonlinear Gauss-Seidel smoother on a coarse
-                               level; units: cells updated */
+                               level, or in the 2D mixed form one tile launch (its passes fused
+                               with the residual and restriction, or with the prolongation);
+                               units: cells updated */
     CHHS_K_RESTRICT = 1,    /* residual + restriction to the next level; units: fine cells */
     CHHS_K_COARSE_RHS = 2,  /* FAS coarse right-hand side; units: coarse cells */
     CHHS_K_PROLONG = 3,     /* prolongation + correction; units: fine cells */
-    CHHS_K_COARSEST = 4,    /* coarsest-grid solve; units: 1 per launch */
+    CHHS_K_COARSEST = 4,    /* the one-block tail: the bottom levels of a V-cycle and the
+                               coarsest-grid solve; units: 1 per launch */
     CHHS_K_NORM = 5,        /* stopping norm on the finest grid; units: cells */
     CHHS_K_FRAME = 6,       /* setup, coefficient restriction, mean of p, accept, and the
                                mixed form's double-precision update; units: launches */
-    CHHS_K_SMOOTH_FINEST = 7, /* the smoother on the finest level; units: cells updated */
+    CHHS_K_SMOOTH_FINEST = 7, /* the smoother (or its tiles) on the finest level; units: cells
+                                 updated */
     CHHS_K_COUNT = 8
 };
 
