@@ -806,7 +806,10 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, in
     if (mode == 0) {
       st->r0 = r;
       st->vcycles = 0;
-      go = (r > st->tol) ? 1u : 0u;
+      if (!isfinite(r))
+        st->failed = 5;  // CHHS_ERR_DIVERGED: a non-finite state or parameter, never "converged"
+      else
+        go = (r > st->tol) ? 1u : 0u;
     } else {
       st->vcycles += 1;
       bool finite = isfinite(r);

@@ -345,3 +345,25 @@ def test_served_3d_extreme_matches_oracle(precision):
         run.set_phi(phi0)
         for _ in range(2):
             _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_non_finite_state_is_reported_and_handle_recovers(precision):
+    """Failure detection without a GPU fault: a NaN in the state makes the
+    step's residual non-finite; the step reports CHHS_ERR_DIVERGED instead of
+    accepting it, leaves phi^m and phi^{m-1} as they were, and the handle
+    works normally once a valid state is set."""
+    shape, h, eps, gamma, dt = (32, 32), 0.1, 0.05, 1.0, 0.01
+    phi0 = inputs.spinodal(shape, 71, mean=0.0, amplitude=0.3)
+    bad = phi0.copy()
+    bad[5, 7] = np.nan
+    with _run(shape, h, eps, gamma, dt, precision) as run:
+        run.set_phi(bad)
+        s, v, r = run.step(2, check=False)
+        assert s == chhs.CHHS_ERR_DIVERGED
+        phim, phimm1, _, _ = run.get_state()
+        assert np.array_equal(phim, bad, equal_nan=True) and np.array_equal(phimm1, bad, equal_nan=True)
+        run.set_phi(phi0)
+        s, v, r = run.step(1)
+        assert s == chhs.CHHS_OK and r <= 1e-10
+        assert np.all(np.isfinite(run.get_phi()))
