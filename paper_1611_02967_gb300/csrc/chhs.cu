@@ -173,6 +173,7 @@ struct chhs {
   // split_threads threads per colour pass use the split update, tiles run
   // tile_threads threads
   int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kTileThreads;
+  int norm_blocks = 1;              // grid of the stopping-norm kernels (whole blocks per SM)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
@@ -434,7 +435,7 @@ struct Enqueue {
   static void norm(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int mode, int use_cond) {
     const Coefs<double> K = coefs<double>(run);
     const Level<double>& L = run->lev[0];
-    const int nb = (L.ncell + kBlock * kNormCells - 1) / (kBlock * kNormCells);
+    const int nb = run->norm_blocks;
     launch(run, s, CHHS_K_NORM, L.ncell, [&] {
       if (mixed(run))
         pdl(k_norm_mixed<DIM>, nb, kBlock, s, L, K, run->lev32[0], run->partials, run->st, cond, mode, use_cond);
@@ -713,6 +714,13 @@ chhs_status setup_handle(chhs_t* run) {
     run->lev32.push_back(make_level<float>(run, Lo.shapes[l], (int)l, run->arena + Lo.level32_off[l], true));
   run->tail_cells = run->opts.precision == 1 ? kTailCellsF32 : kTailCellsF64;
   place_tail(run);
+  // The norm kernels loop over cells with the grid's stride: kNormBlocksPerSM
+  // blocks on every SM (all resident at once), so no SM holds a block more
+  // than another; small grids take one cell per thread.
+  int dev = 0, nsm = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  run->norm_blocks = std::max(1, std::min(nblocks(run->ncell()), kNormBlocksPerSM * nsm));
   CU(cudaMemsetAsync(run->arena, 0, Lo.total, run->stream));
   CU(cudaMallocHost(&run->host_st, sizeof(DevState)));
   memset(run->host_st, 0, sizeof(DevState));

@@ -27,7 +27,6 @@
 namespace chhs_dev {
 
 constexpr int kBlock = 256;        // block size of the plain per-cell kernels
-constexpr int kNormCells = 4;      // cells per thread of the norm kernels (amortises their block sums)
 constexpr int kSmoothBlock = 128;  // block size of the smoother (more, smaller blocks per SM)
 constexpr int kTailThreads = 512;  // one block runs the coarse tail of a V-cycle
 constexpr int kTailMaxLevels = 12;
@@ -825,6 +824,11 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, in
   return go;
 }
 
+// Blocks per SM of the norm kernels; their threads loop over cells with the
+// grid's stride, which amortises the double-precision block sums, and every SM
+// holds the same number of blocks.
+constexpr int kNormBlocksPerSM = 2;
+
 // Stopping norm sqrt(mean over cells of r_phi^2 + r_mu^2 + (s r_p)^2) on the
 // finest grid, in one launch: every block writes its partial sums, and the
 // last block to finish (ticket counter) adds the partials in a fixed order and
@@ -836,11 +840,8 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
   pdl_enter();
   __shared__ bool last;
   double acc[2] = {0.0, 0.0};
-  const int base = blockIdx.x * blockDim.x * kNormCells + threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < kNormCells; ++q) {
-    const int c = base + q * blockDim.x;
-    if (c >= L.ncell) break;
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += stride) {
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
     T n1, n2, n3;
@@ -927,11 +928,8 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
   pdl_enter();
   __shared__ bool last;
   double acc[2] = {0.0, 0.0};
-  const int base = blockIdx.x * blockDim.x * kNormCells + threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < kNormCells; ++q) {
-    const int c = base + q * blockDim.x;
-    if (c >= L.ncell) break;
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += stride) {
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
     double n1, n2, n3;
