@@ -61,6 +61,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-request-loop", action="store_true",
+                    help="skip the served and batched legs (for profiler runs: their request loops "
+                         "launch for minutes under a profiler)")
     return ap.parse_args(argv)
 
 
@@ -489,8 +492,10 @@ def run_ours(args):
              "max_abs_phi_diff_vs_f64_after_K_steps": diff}
     run32.close()
 
-    served = served_leg(mixed["value"] / world)
-    batched = batched_leg()
+    served = batched = None
+    if not args.no_request_loop:
+        served = served_leg(mixed["value"] / world)
+        batched = batched_leg()
     bubbles = bubbles_leg(stream, flush)
 
     cpu = None
