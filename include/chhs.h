@@ -79,9 +79,12 @@ size_t chhs_workspace_bytes(int dim, const int n[3], const chhs_opts* opts);
  * single level of 4,225 cells; the limit is about 1,000 cells in double
  * precision, 2,000 in the mixed form) is rejected with CHHS_ERR_INVALID_ARG,
  * as are opts with sweep counts too large for the mixed form's tiles.
- * Errors: CHHS_ERR_INVALID_ARG (dim not 2 or 3, an extent < 2, h, eps or dt
- * <= 0, gamma < 0, invalid opts, the cases above), CHHS_ERR_OOM,
- * CHHS_ERR_CUDA. */
+ * Errors: CHHS_ERR_INVALID_ARG (out or n NULL, dim not 2 or 3, an extent
+ * < 2 or > 2^20, more than 2^28 cells, h, eps or dt <= 0, gamma < 0, a
+ * non-finite h, eps, gamma or dt, invalid opts -- nu1 or nu2 < 0, nu1 + nu2
+ * < 1, max_v < 1, coarsest < 1, tol not > 0, precision not 0 or 1 -- and
+ * the cases above; these are checked before any CUDA call), CHHS_ERR_OOM,
+ * CHHS_ERR_CUDA (for instance, no usable GPU). */
 chhs_status chhs_create(int dim, const int n[3], double h, double eps, double gamma, double dt,
                         const chhs_opts* opts, void* cuda_stream, chhs_t** out);
 
@@ -280,7 +283,9 @@ chhs_status chhs_server_create(size_t pool_bytes, int max_active, int steps_per_
 chhs_status chhs_server_submit(chhs_server_t* sv, const chhs_request* req, long long* id_out);
 
 /* Block until run id is done or timeout_s seconds pass (then
- * CHHS_ERR_NOT_CONVERGED is returned and the run keeps going). */
+ * CHHS_ERR_NOT_CONVERGED is returned and the run keeps going).  timeout_s
+ * above 1e6 (infinity included) waits without a limit; a negative or NaN
+ * timeout_s, an unknown id or a NULL server give CHHS_ERR_INVALID_ARG. */
 chhs_status chhs_server_wait(chhs_server_t* sv, long long id, double timeout_s);
 
 /* Result of run id: *done = 0 while it runs; when done, its status, V-cycles

@@ -311,12 +311,20 @@ chhs_status chhs_server_stats(chhs_server_t* sv, int* queued, int* active, int* 
 }
 
 chhs_status chhs_server_wait(chhs_server_t* sv, long long id, double timeout_s) {
-  if (!sv) return CHHS_ERR_INVALID_ARG;
+  if (!sv || !(timeout_s >= 0)) return CHHS_ERR_INVALID_ARG;  // negative or NaN
   std::unique_lock<std::mutex> lk(sv->mu);
   auto it = sv->all.find(id);
   if (it == sv->all.end()) return CHHS_ERR_INVALID_ARG;
   Job* j = it->second;
-  bool ok = sv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] { return j->done; });
+  auto done = [&] { return j->done; };
+  // A limit past kNoLimitS (about 11.6 days; infinity included) waits without
+  // one: converting a larger one to the clock's integer ticks could overflow.
+  constexpr double kNoLimitS = 1e6;
+  if (timeout_s > kNoLimitS) {
+    sv->cv.wait(lk, done);
+    return CHHS_OK;
+  }
+  bool ok = sv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), done);
   return ok ? CHHS_OK : CHHS_ERR_NOT_CONVERGED;
 }
 
