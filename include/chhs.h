@@ -289,12 +289,16 @@ chhs_status chhs_server_submit(chhs_server_t* sv, const chhs_request* req, long 
 chhs_status chhs_server_wait(chhs_server_t* sv, long long id, double timeout_s);
 
 /* Result of run id: *done = 0 while it runs; when done, its status, V-cycles
- * summed over its steps, phi at its last step (host, n cells; nullable) and
- * times3 = {submit, admit, done} in seconds of a monotonic clock (nullable). */
+ * summed over its steps, phi at its last step (host, n cells; nullable; NaN
+ * in every cell for a run refused before it held a state, e.g. one whose
+ * hierarchy exceeds the whole pool) and times3 = {submit, admit, done} in
+ * seconds of a monotonic clock (nullable). */
 chhs_status chhs_server_result(chhs_server_t* sv, long long id, int* done, int* status, int* vcycles,
                                double* phi_out, double* times3);
 
-/* Forget a finished run's result. */
+/* Forget a finished run's result (CHHS_ERR_INVALID_ARG for a run not yet
+ * done or an unknown id).  A thread waiting on the run in chhs_server_wait
+ * returns CHHS_OK. */
 chhs_status chhs_server_release(chhs_server_t* sv, long long id);
 
 /* Runs waiting, on the GPU and finished, and pool bytes in use (each nullable). */

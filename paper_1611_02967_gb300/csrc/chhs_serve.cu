@@ -19,6 +19,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -313,10 +314,14 @@ chhs_status chhs_server_stats(chhs_server_t* sv, int* queued, int* active, int* 
 chhs_status chhs_server_wait(chhs_server_t* sv, long long id, double timeout_s) {
   if (!sv || !(timeout_s >= 0)) return CHHS_ERR_INVALID_ARG;  // negative or NaN
   std::unique_lock<std::mutex> lk(sv->mu);
-  auto it = sv->all.find(id);
-  if (it == sv->all.end()) return CHHS_ERR_INVALID_ARG;
-  Job* j = it->second;
-  auto done = [&] { return j->done; };
+  if (sv->all.find(id) == sv->all.end()) return CHHS_ERR_INVALID_ARG;
+  // Looked up again at every wake-up: another thread may release the run
+  // (which needs it done) between the worker's notify and this thread
+  // taking the lock back, and the Job is then gone.
+  auto done = [&] {
+    auto f = sv->all.find(id);
+    return f == sv->all.end() || f->second->done;
+  };
   // A limit past kNoLimitS (about 11.6 days; infinity included) waits without
   // one: converting a larger one to the clock's integer ticks could overflow.
   constexpr double kNoLimitS = 1e6;
@@ -339,7 +344,14 @@ chhs_status chhs_server_result(chhs_server_t* sv, long long id, int* done, int* 
   if (!j->done) return CHHS_OK;
   if (status) *status = j->status;
   if (vcycles) *vcycles = j->vcycles;
-  if (phi_out && !j->phi_out.empty()) memcpy(phi_out, j->phi_out.data(), sizeof(double) * j->phi_out.size());
+  if (phi_out) {
+    if (!j->phi_out.empty()) {
+      memcpy(phi_out, j->phi_out.data(), sizeof(double) * j->phi_out.size());
+    } else {  // refused before it held a state (admission): no phi to report
+      size_t n = (size_t)j->req.n[0] * j->req.n[1] * (j->req.dim == 3 ? j->req.n[2] : 1);
+      std::fill(phi_out, phi_out + n, std::numeric_limits<double>::quiet_NaN());
+    }
+  }
   if (times3) {
     times3[0] = j->t_submit;
     times3[1] = j->t_admit;

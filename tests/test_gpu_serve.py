@@ -71,4 +71,6 @@ def test_admission_by_memory_and_oom():
             time.sleep(0.001)
         assert 1 <= peak <= 2  # never more runs than the pool holds
         assert all(sv.result(r)["status"] == chhs.CHHS_OK for r in ids)
-        assert sv.result(big)["status"] == chhs.CHHS_ERR_OOM
+        res = sv.result(big)
+        assert res["status"] == chhs.CHHS_ERR_OOM
+        assert np.isnan(res["phi"]).all()  # refused at admission: it never held a state
