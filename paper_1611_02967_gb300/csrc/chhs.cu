@@ -910,6 +910,8 @@ chhs_status chhs_launch_counts(const chhs_t* run, int* per_vcycle, int* per_step
 
 chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_out, double* units_out) {
   if (!run || !ms_out || !launches_out || !units_out) return fail(run, CHHS_ERR_INVALID_ARG, "NULL argument");
+  // it resets the step counters, which would drop a pending step's status
+  if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   run->err.clear();
   Prof prof;
   run->prof = &prof;
