@@ -91,7 +91,9 @@ chhs_status chhs_create(int dim, const int n[3], double h, double eps, double ga
 /* As chhs_create, but the hierarchy lives in the caller's device buffer
  * `arena` of `arena_bytes` (>= chhs_workspace_bytes, 256-byte aligned), which
  * must outlive the handle.  The handle allocates no device memory of its own
- * apart from its CUDA graph. */
+ * apart from its CUDA graph.  Errors as chhs_create, and, checked before any
+ * CUDA call, CHHS_ERR_INVALID_ARG for a NULL or misaligned arena and
+ * CHHS_ERR_OOM for one smaller than chhs_workspace_bytes. */
 chhs_status chhs_create_ext(int dim, const int n[3], double h, double eps, double gamma, double dt,
                             const chhs_opts* opts, void* cuda_stream, void* arena, size_t arena_bytes,
                             chhs_t** out);

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/chhs.h"
@@ -739,13 +740,19 @@ chhs_status create_impl(int dim, const int n[3], double h, double eps, double ga
   chhs_default_opts(&o);
   if (opts) o = *opts;
   if (!valid_problem(dim, n, h, eps, gamma, dt) || !valid_opts(o)) return CHHS_ERR_INVALID_ARG;
+  const int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  Layout layout = make_layout(dim, nn, o.coarsest, o.precision);
+  if (arena) {  // the caller's arena is checked before any CUDA call
+    if (reinterpret_cast<uintptr_t>(arena) % kAlign != 0) return CHHS_ERR_INVALID_ARG;
+    if (arena_bytes < layout.total) return CHHS_ERR_OOM;
+  }
   chhs_t* run = new (std::nothrow) chhs_t();
   if (!run) return CHHS_ERR_OOM;
   run->dim = dim;
-  for (int a = 0; a < 3; ++a) run->n[a] = (a < dim) ? n[a] : 1;
+  for (int a = 0; a < 3; ++a) run->n[a] = nn[a];
   run->h = h; run->eps = eps; run->gamma = gamma; run->dt = dt;
   run->opts = o;
-  run->layout = make_layout(dim, run->n, o.coarsest, o.precision);
+  run->layout = std::move(layout);
   chhs_status s = CHHS_OK;
   if (cuda_stream) {
     run->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -757,10 +764,6 @@ chhs_status create_impl(int dim, const int n[3], double h, double eps, double ga
     run->own_stream = true;
   }
   if (arena) {
-    if (arena_bytes < run->layout.total || (reinterpret_cast<uintptr_t>(arena) % kAlign) != 0) {
-      chhs_destroy(run);
-      return CHHS_ERR_OOM;
-    }
     run->arena = static_cast<char*>(arena);
   } else {
     if (cudaMalloc(&run->arena, run->layout.total) != cudaSuccess) {

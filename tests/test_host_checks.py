@@ -168,6 +168,19 @@ def _gpu_present():
     return torch.cuda.is_available()
 
 
+@pytest.mark.skipif(_gpu_present(), reason="passes addresses that are not device memory")
+def test_create_ext_arena_checks(L):
+    # misaligned or too small: refused before any CUDA call, so these
+    # addresses (never dereferenced) are safe here
+    need = L.chhs_workspace_bytes(2, _n(16, 16), None)
+    out = ctypes.c_void_p(12345)
+    args = (2, _n(16, 16), 0.025, 0.05, 1.0, 0.005, None, None)
+    assert L.chhs_create_ext(*args, ctypes.c_void_p(0x10010), need, ctypes.byref(out)) == INVALID
+    assert out.value is None
+    assert L.chhs_create_ext(*args, ctypes.c_void_p(0x10000), need - 1, ctypes.byref(out)) == chhs.CHHS_ERR_OOM
+    assert out.value is None
+
+
 @pytest.mark.skipif(_gpu_present(), reason="checks the behaviour without a usable GPU")
 def test_no_gpu_fails_loudly(L):
     # valid arguments, no GPU: CHHS_ERR_CUDA and no handle, never a CPU path
