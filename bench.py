@@ -145,7 +145,13 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = [r for r in self.rows if len(r) >= 9]
+        return self.summarize(self.rows)
+
+    @staticmethod
+    def summarize(rows):
+        """Median SM clock, the maximum clock and the throttle reasons seen
+        active in nvidia-smi rows of FIELDS (values split, no header)."""
+        rows = [r for r in rows if len(r) >= 9]
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
