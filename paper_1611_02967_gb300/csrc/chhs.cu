@@ -563,7 +563,8 @@ struct Enqueue {
     norm(run, cs, cond, 0, 1);
     CU(cudaStreamWaitEvent(cs, join, 0));
     CU(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps));
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cudaGraphNodeParams cp{};  // every other field zero
+    cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
