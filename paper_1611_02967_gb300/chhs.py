@@ -320,7 +320,7 @@ class Run:
         devs = {b[1] for b in bufs if b[0] is not None}
         if len(devs) > 1:
             raise ValueError("mixed host and device buffers")
-        self._check(lib().chhs_set_state(self.handle, *[b[0] for b in bufs], devs.pop()))
+        self._check(lib().chhs_set_state(self.handle, *[b[0] for b in bufs], devs.pop() if devs else 0))
 
 
 class Server:

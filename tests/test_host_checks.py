@@ -192,3 +192,31 @@ def test_no_gpu_fails_loudly(L):
     sv = ctypes.c_void_p(12345)
     assert L.chhs_server_create(1 << 30, 4, 5, ctypes.byref(sv)) == chhs.CHHS_ERR_CUDA
     assert sv.value is None
+
+
+def test_binding_buffer_checks():
+    # the binding's marshalling of host buffers (chhs._buf): what it copies,
+    # what it refuses
+    import numpy as np
+    import torch
+
+    a = np.arange(12, dtype=np.float64).reshape(3, 4)
+    p, dev, keep = chhs._buf(a, 12)
+    assert dev == 0 and keep is a and p.value == a.ctypes.data  # no copy
+    f32 = a.astype(np.float32)
+    p, dev, keep = chhs._buf(f32, 12)
+    assert keep.dtype == np.float64 and np.array_equal(keep, a)  # converted copy for inputs
+    with pytest.raises(ValueError):
+        chhs._buf(f32, 12, writable=True)  # an output must be written in place
+    with pytest.raises(ValueError):
+        chhs._buf(a.T, 12, writable=True)  # not C-contiguous
+    with pytest.raises(ValueError):
+        chhs._buf(a, 13)
+    t = torch.zeros(12, dtype=torch.float64)
+    p, dev, keep = chhs._buf(t, 12)
+    assert dev == 0 and p.value == t.data_ptr()
+    with pytest.raises(ValueError):
+        chhs._buf(torch.zeros(12, dtype=torch.float32), 12)
+    with pytest.raises(ValueError):
+        chhs._buf(torch.zeros(24, dtype=torch.float64)[::2], 12)  # strided view
+    assert chhs._buf(None, 12) == (None, 0, None)
