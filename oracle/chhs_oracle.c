@@ -218,6 +218,9 @@ static void restrict_mean(const level_t* F, const level_t* C, const double* fine
 
 /* ---------------------------------------------------------------- FAS */
 
+/* The coarsest grid (the Section 5 preamble's "2x2", read as the coarsest
+ * level): the smoother repeated until the residual has fallen by 1e-13 or
+ * stops falling, then the pressure gauge. */
 static void coarse_solve(level_t* L, const params_t* P) {
     double r0 = residual(L, P), prev = r0;
     for (int it = 0; it < 2000; ++it) {
@@ -230,6 +233,9 @@ static void coarse_solve(level_t* L, const params_t* P) {
     remove_mean(L->p, L->ncell);
 }
 
+/* One FAS V(nu1, nu2)-cycle from level l (Section 5 preamble): pre-smooth,
+ * restrict the iterate and the residual, coarse right-hand side
+ * R r + N_c(R u), recurse, add the prolonged coarse correction, post-smooth. */
 static void vcycle(level_t* lev, int l, int nlev, const params_t* P) {
     level_t* L = &lev[l];
     if (l == nlev - 1) {
