@@ -34,6 +34,7 @@ def _prm(h, eps, gamma, s, tol=1e-13):
     ((8, 8), 0.4, 0.2, 4.0, 0.1),
     ((4, 4, 4), 0.4, 0.1, 2.0, 0.02),
     ((2, 2), 0.5, 0.2, 1.0, 0.01),
+    ((8, 16), 0.3, 0.15, 0.0, 0.05),
 ])
 def test_fas_matches_dense_newton(shape, h, eps, gamma, s):
     phim = inputs.spinodal(shape, 11, mean=0.1, amplitude=0.6)
