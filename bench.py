@@ -64,7 +64,43 @@ def parse_args(argv=None):
     ap.add_argument("--no-request-loop", action="store_true",
                     help="skip the served and batched legs (for profiler runs: their request loops "
                          "launch for minutes under a profiler)")
+    ap.add_argument("--profile-run", choices=PROFILE_RUNS, default=None,
+                    help="for profiler captures: only W graph steps of one workload and form, then K steps "
+                         "launched kernel by kernel (chhs_profile_step, which a profiler can see), and a "
+                         "JSON line of the per-kernel-kind device times")
     return ap.parse_args(argv)
+
+
+PROFILE_RUNS = ["spinodal512-f64", "spinodal512-mixed", "bubbles128-f64", "bubbles128-mixed",
+                "spinodal64-f64", "spinodal64-mixed"]
+
+
+def profile_run(args):
+    """W steps through the step graph, then K steps launched kernel by kernel
+    with CUDA events (the form profilers can capture: they do not see inside
+    a graph with a conditional node); prints the per-kind times."""
+    import torch
+
+    from paper_1611_02967_gb300 import chhs, inputs
+    name, form = args.profile_run.rsplit("-", 1)
+    w = inputs.workload(name)
+    run = chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"],
+                   opts=chhs.default_opts(precision=1 if form == "mixed" else 0))
+    run.set_phi(w["phi0"])
+    if args.warmup:
+        run.step(args.warmup)
+    prof = None
+    for _ in range(args.steps):
+        prof = run.profile_step(prof)
+    torch.cuda.synchronize()
+    total = sum(v[0] for v in prof.values())
+    print(json.dumps({"profile_run": args.profile_run, "steps": args.steps, "ms_per_step": total / args.steps,
+                      "kernels": {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / total,
+                                      "launches_per_step": v[1] / args.steps,
+                                      "us_per_launch": 1e3 * v[0] / v[1] if v[1] else None}
+                                  for k, v in prof.items()}}), flush=True)
+    run.close()
+    return 0
 
 
 def dist_env():
@@ -529,6 +565,8 @@ def run_ours(args):
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_run:
+        return profile_run(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -54,10 +54,16 @@ typedef struct {
     int nu1;       /* pre-smoothing sweeps per level (default 2) */
     int nu2;       /* post-smoothing sweeps per level (default 2) */
     int max_v;     /* V-cycles per step before CHHS_ERR_NOT_CONVERGED (default 50) */
-    int coarsest;  /* coarsening stops before a direction would drop below this (default 2) */
+    int coarsest;  /* coarsening stops before a direction would drop below this (default 2, at least 2) */
     double tol;    /* stopping norm: sqrt(mean over cells of r_phi^2 + r_mu^2 + (s r_p)^2) (default 1e-10) */
     int precision; /* 0: double-precision V-cycles; 1: single-precision V-cycles inside a
                       double-precision defect-correction loop (same tol, measured in double) */
+    double max_factor; /* pointwise guard: a step is also held until the largest residual,
+                          max over cells of max(|r_phi|, |r_mu|, |s r_p|), is at most
+                          max_factor * tol (default 10; 0 turns the guard off).  The mean-square
+                          norm alone lets a residual concentrated in a few cells (thin
+                          interfaces) leave a pointwise error in phi of ~15 tol; the guard
+                          bounds it by about 0.4 max_factor tol. */
 } chhs_opts;
 
 /* Fill *opts with the defaults above.  Returns CHHS_ERR_INVALID_ARG on NULL. */
@@ -82,7 +88,8 @@ size_t chhs_workspace_bytes(int dim, const int n[3], const chhs_opts* opts);
  * Errors: CHHS_ERR_INVALID_ARG (out or n NULL, dim not 2 or 3, an extent
  * < 2 or > 2^20, more than 2^28 cells, h, eps or dt <= 0, gamma < 0, a
  * non-finite h, eps, gamma or dt, invalid opts -- nu1 or nu2 < 0, nu1 + nu2
- * < 1, max_v < 1, coarsest < 1, tol not > 0, precision not 0 or 1 -- and
+ * < 1, max_v < 1, coarsest < 2, tol not > 0, precision not 0 or 1,
+ * max_factor < 0 or NaN -- and
  * the cases above; these are checked before any CUDA call), CHHS_ERR_OOM,
  * CHHS_ERR_CUDA (for instance, no usable GPU). */
 chhs_status chhs_create(int dim, const int n[3], double h, double eps, double gamma, double dt,
@@ -170,7 +177,9 @@ typedef struct {
   int split_threads;  /* double-precision levels with at most this many cells per colour
                          use the three-warp split update (0: never) */
   int tile_threads;   /* threads per tile in the 2D mixed form */
-  double ms_per_step; /* the chosen setting's time per step in the trials */
+  double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
+                         the setting in force was timed (every candidate failed, or the fastest
+                         could not be rebuilt and the original setting was kept) */
 } chhs_tuning;
 
 /* Autotuner of the handle's launch shapes: tries candidate settings (where
@@ -238,20 +247,23 @@ chhs_status chhs_set_state(chhs_t* run, const double* phi, const double* phi_pre
  *
  * phi_dev, psi_dev: device pointers to dim-dimensional grids of n[0] x n[1]
  * (x n[2]) doubles, x fastest (psi_dev NULL means psi = phi).  Outputs
- * (nullable host pointers): mass_out = (phi, 1), E_out = E_h(phi) (Eq. 2.8),
- * F_out = F_h(phi, psi) (Eq. 2.9), the same quantities chhs_mass and
- * chhs_energy report for a handle's phi^m and phi^{m-1}.  Work is ordered
- * on cuda_stream (NULL = the legacy default stream); the call waits for it.
+ * (nullable host pointers): mass_out, E_out and F_out, the same three
+ * quantities that chhs_mass and chhs_energy report for a handle's phi^m and
+ * phi^{m-1}, here for phi and psi.  Work is ordered on cuda_stream (NULL =
+ * the legacy default stream), and the call waits for that stream to finish
+ * before it returns (the sums are read back to the host).
  *
  * Scratch: a fixed device array of about 0.8 MB inside the library, held by
  * every GPU that loads it until the process exits; grids above
  * CHHS_NOALLOC_MAX_CELLS cells return CHHS_ERR_INVALID_ARG, as do a
  * dimension other than 2 or 3, a size below 1, h <= 0 or eps <= 0.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call outside any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one array: calls that overlap on the GPU (on different
  * streams, or from several host threads) race and must be serialised by the
- * caller.  Returns CHHS_ERR_CUDA if a CUDA call fails. */
+ * caller.  Returns CHHS_ERR_CUDA if a CUDA call fails; a launch failure is
+ * read with cudaGetLastError, which also reports (and clears) an error that
+ * an earlier, unrelated launch left on the calling thread. */
 chhs_status chhs_energy_noalloc(int dim, const int n[3], double h, double eps, const double* phi_dev,
                                 const double* psi_dev, void* cuda_stream, double* mass_out,
                                 double* E_out, double* F_out);

@@ -117,9 +117,12 @@ Layout make_layout(int dim, const int n[3], int coarsest, int precision) {
   return L;
 }
 
+// coarsest >= 2: a level of one cell per direction has no interior face, so
+// its Newton diagonal and the pressure row have nothing to work with (the
+// pressure problem is singular and the face count 0 has no inverse).
 bool valid_opts(const chhs_opts& o) {
-  return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.max_v >= 1 && o.coarsest >= 1 &&
-         o.tol > 0 && (o.precision == 0 || o.precision == 1);
+  return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.max_v >= 1 && o.coarsest >= 2 &&
+         o.tol > 0 && (o.precision == 0 || o.precision == 1) && o.max_factor >= 0;
 }
 
 bool valid_problem(int dim, const int n[3], double h, double eps, double gamma, double dt) {
@@ -634,12 +637,18 @@ struct Enqueue {
   }
 };
 
-__global__ void k_reset_call(DevState* st, double tol, int max_v) {
+__global__ void k_reset_call(DevState* st, double tol, double tol_max, int max_v) {
   st->failed = 0;
   st->vtotal = 0;
   st->steps_done = 0;
   st->tol = tol;
+  st->tol_max = tol_max;
   st->max_v = max_v;
+}
+
+// The pointwise guard's bound (infinite when the guard is off).
+double tol_max_of(const chhs_opts& o) {
+  return o.max_factor > 0 ? o.max_factor * o.tol : INFINITY;
 }
 
 // The arrays of one level, carved out of the arena at base.
@@ -810,6 +819,7 @@ chhs_status chhs_default_opts(chhs_opts* o) {
   o->coarsest = 2;
   o->tol = 1e-10;
   o->precision = 0;
+  o->max_factor = 10.0;
   return CHHS_OK;
 }
 
@@ -869,7 +879,7 @@ chhs_status chhs_step_async(chhs_t* run, int nsteps) {
   if (nsteps < 0) return fail(run, CHHS_ERR_INVALID_ARG, "nsteps < 0");
   run->err.clear();
   if (!run->pending) {  // the first call since the last wait starts a new count
-    k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, run->opts.max_v);
+    k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, tol_max_of(run->opts), run->opts.max_v);
     CU(cudaGetLastError());
     run->pending = true;
   }
@@ -919,7 +929,7 @@ chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_o
   run->err.clear();
   Prof prof;
   run->prof = &prof;
-  k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, run->opts.max_v);
+  k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, tol_max_of(run->opts), run->opts.max_v);
   chhs_status s = run->dim == 2 ? Enqueue<2>::profile_step(run) : Enqueue<3>::profile_step(run);
   run->prof = nullptr;
   if (s != CHHS_OK) return s;
@@ -1058,7 +1068,10 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   }
   run->err.clear();
   if ((s = apply(best)) != CHHS_OK) {
+    // the fastest setting could not be rebuilt: the original one is kept, and
+    // its time is not the one measured for the best candidate
     if (apply(orig) != CHHS_OK) return fail(run, CHHS_ERR_CUDA, "could not rebuild the step graph");
+    best_ms = -1.f;
   }
   if ((s = restore()) != CHHS_OK) return s;
   CU(cudaStreamSynchronize(run->stream));

@@ -70,7 +70,9 @@ struct DevState {
   int max_v;
   int go;          // 1 while another V-cycle is due (mirror of the loop condition)
   double tol;
+  double tol_max;  // bound of the pointwise guard (infinite when it is off)
   double resid;    // last fine-grid stopping norm
+  double rmax;     // last fine-grid pointwise residual max(|r_phi|, |r_mu|, |s r_p|)
   double r0;       // stopping norm at the start of the step
   double pmean;    // mean of p, removed when the step is accepted
   double diag[8];  // reduction results (mass, energies)
@@ -796,11 +798,15 @@ __device__ __forceinline__ void sum_partials(const double* partials, int nparts,
   block_sum<NV>(tot);
 }
 
-// The loop decision after a norm r.  mode 0: start of a step (records r0);
-// mode 1: after a V-cycle (counts it).  Returns 1 while another cycle is due.
-__device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, int mode) {
+// The loop decision after a norm r and a pointwise residual rmax.  mode 0:
+// start of a step (records r0); mode 1: after a V-cycle (counts it).  The
+// step is converged when r <= tol and rmax <= tol_max.  Returns 1 while
+// another cycle is due.
+__device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, double rmax, int mode) {
   st->resid = r;
+  st->rmax = rmax;
   unsigned int go = 0;
+  const bool above = r > st->tol || rmax > st->tol_max;
   if (st->failed == 0) {
     if (mode == 0) {
       st->r0 = r;
@@ -808,13 +814,13 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, in
       if (!isfinite(r))
         st->failed = 5;  // CHHS_ERR_DIVERGED: a non-finite state or parameter, never "converged"
       else
-        go = (r > st->tol) ? 1u : 0u;
+        go = above ? 1u : 0u;
     } else {
       st->vcycles += 1;
       bool finite = isfinite(r);
       if (!finite || r > 1e8 * (st->r0 + 1.0)) {
         st->failed = 5;  // CHHS_ERR_DIVERGED
-      } else if (r > st->tol) {
+      } else if (above) {
         if (st->vcycles >= st->max_v) st->failed = 4;  // CHHS_ERR_NOT_CONVERGED
         else go = 1u;
       }
@@ -822,6 +828,43 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, in
   }
   st->go = (int)go;
   return go;
+}
+
+// Largest of the three rows' residuals at a cell (the pointwise guard).
+__device__ __forceinline__ double row_max(double r1, double r2, double r3s) {
+  return fmax(fmax(fabs(r1), fabs(r2)), fabs(r3s));
+}
+
+// Block maximum of v (v >= 0); thread 0 returns it.
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double shm[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, shm[w]);
+  __syncthreads();
+  return v;
+}
+
+// The norm kernels' last block: the partials (sum of squares, sum of p,
+// largest pointwise residual per block) in a fixed order, then the decision.
+__device__ __forceinline__ void norm_finish(const double* partials, int nparts, int ncell, DevState* st,
+                                            cudaGraphConditionalHandle cond, int mode, int use_cond) {
+  double tot[2] = {0.0, 0.0};
+  double mx = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    tot[0] += __ldcg(partials + 3 * b);
+    tot[1] += __ldcg(partials + 3 * b + 1);
+    mx = fmax(mx, __ldcg(partials + 3 * b + 2));
+  }
+  block_sum<2>(tot);
+  mx = block_max(mx);
+  if (threadIdx.x != 0) return;
+  st->ticket = 0;
+  st->pmean = tot[1] / ncell;
+  unsigned int go = loop_decision(st, sqrt(tot[0] / ncell), mx, mode);
+  if (use_cond) cudaGraphSetConditional(cond, go);
 }
 
 // Blocks per SM of the norm kernels; their threads loop over cells with the
@@ -840,6 +883,7 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
   pdl_enter();
   __shared__ bool last;
   double acc[2] = {0.0, 0.0};
+  double mx = 0.0;
   const int stride = gridDim.x * blockDim.x;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += stride) {
     int i, j, k;
@@ -852,24 +896,21 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
     acc[0] = fma(r2, r2, acc[0]);
     acc[0] = fma(r3, r3, acc[0]);
     acc[1] += double(L.p[c]);
+    mx = fmax(mx, row_max(r1, r2, r3));
   }
   block_sum<2>(acc);
+  mx = block_max(mx);
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = acc[0];
-    partials[2 * blockIdx.x + 1] = acc[1];
+    partials[3 * blockIdx.x] = acc[0];
+    partials[3 * blockIdx.x + 1] = acc[1];
+    partials[3 * blockIdx.x + 2] = mx;
     __threadfence();
     last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot[2];
-  sum_partials<2>(partials, gridDim.x, tot);
-  if (threadIdx.x != 0) return;
-  st->ticket = 0;
-  st->pmean = tot[1] / L.ncell;
-  unsigned int go = loop_decision(st, sqrt(tot[0] / L.ncell), mode);
-  if (use_cond) cudaGraphSetConditional(cond, go);
+  norm_finish(partials, gridDim.x, L.ncell, st, cond, mode, use_cond);
 }
 
 // ---------------------------------------------------------------- mixed precision
@@ -928,6 +969,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
   pdl_enter();
   __shared__ bool last;
   double acc[2] = {0.0, 0.0};
+  double mx = 0.0;
   const int stride = gridDim.x * blockDim.x;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += stride) {
     int i, j, k;
@@ -940,6 +982,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
     acc[0] = fma(r2, r2, acc[0]);
     acc[0] = fma(r3s, r3s, acc[0]);
     acc[1] += L.p[c];
+    mx = fmax(mx, row_max(r1, r2, r3s));
     G.fphi[c] = f64_to_f32_rz(r1);
     G.fmu[c] = f64_to_f32_rz(r2);
     G.fp[c] = f64_to_f32_rz(r3);
@@ -949,22 +992,18 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
     G.phib[c] = f64_to_f32_rz(L.phi[c]);
   }
   block_sum<2>(acc);
+  mx = block_max(mx);
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = acc[0];
-    partials[2 * blockIdx.x + 1] = acc[1];
+    partials[3 * blockIdx.x] = acc[0];
+    partials[3 * blockIdx.x + 1] = acc[1];
+    partials[3 * blockIdx.x + 2] = mx;
     __threadfence();
     last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot[2];
-  sum_partials<2>(partials, gridDim.x, tot);
-  if (threadIdx.x != 0) return;
-  st->ticket = 0;
-  st->pmean = tot[1] / L.ncell;
-  unsigned int go = loop_decision(st, sqrt(tot[0] / L.ncell), mode);
-  if (use_cond) cudaGraphSetConditional(cond, go);
+  norm_finish(partials, gridDim.x, L.ncell, st, cond, mode, use_cond);
 }
 
 // u <- u + e in double precision.

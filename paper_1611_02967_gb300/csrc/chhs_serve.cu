@@ -144,10 +144,10 @@ struct chhs_server {
       if (!arena) {
         if (active.empty() && need) {  // can never fit: fail it rather than block the queue
           queue.pop_front();
-          j->status = CHHS_ERR_OOM;
-          j->done = true;
-          j->t_admit = j->t_done = now_s();
-          ++n_done;
+          j->t_admit = now_s();
+          teardown(j);  // no device resources yet: frees the host copies only
+          record_locked(j, CHHS_ERR_OOM);
+          cv.notify_all();
           continue;
         }
         return;  // wait for memory to free up
@@ -167,9 +167,11 @@ struct chhs_server {
         s = chhs_set_phi(j->run, j->phi0.data(), j->phi_prev.empty() ? nullptr : j->phi_prev.data(), 0);
       j->steps_left = j->req.nsteps;
       if (s == CHHS_OK) s = launch_slice(j);
+      if (s != CHHS_OK) teardown(j);
       lk.lock();
       if (s != CHHS_OK) {
-        finish_locked(j, s);
+        record_locked(j, s);
+        cv.notify_all();
         continue;
       }
       active.push_back(j);
@@ -185,9 +187,12 @@ struct chhs_server {
     return CHHS_OK;
   }
 
-  // Release a job's device resources and record its result (lock held).
-  void finish_locked(Job* j, int status) {
-    j->status = status;
+  // A finished job's device side: copy phi out, destroy its handle, stream
+  // and event.  Called without the lock (only the worker thread, or the
+  // destroying thread once the worker has stopped, touches a job's device
+  // resources), so a long copy-out does not hold up the other runs' slices
+  // or the callers of submit, stats and result.
+  void teardown(Job* j) {
     if (j->run) {
       size_t n = (size_t)j->req.n[0] * j->req.n[1] * (j->req.dim == 3 ? j->req.n[2] : 1);
       j->phi_out.resize(n);
@@ -199,15 +204,28 @@ struct chhs_server {
     if (j->stream) cudaStreamDestroy(j->stream);
     j->slice_done = nullptr;
     j->stream = nullptr;
+    j->phi0.clear();
+    j->phi0.shrink_to_fit();
+    j->phi_prev.clear();
+    j->phi_prev.shrink_to_fit();
+  }
+
+  // Return a torn-down job's memory to the pool and publish its result (lock held).
+  void record_locked(Job* j, int status) {
+    j->status = status;
     if (j->arena) pool.release(j->arena);
     j->arena = nullptr;
     j->done = true;
     j->t_done = now_s();
     ++n_done;
-    j->phi0.clear();
-    j->phi0.shrink_to_fit();
-    j->phi_prev.clear();
-    j->phi_prev.shrink_to_fit();
+  }
+
+  // Tear a job down and record it, dropping the lock for the device work.
+  void finish(std::unique_lock<std::mutex>& lk, Job* j, int status) {
+    lk.unlock();
+    teardown(j);
+    lk.lock();
+    record_locked(j, status);
   }
 
   void loop() {
@@ -234,8 +252,10 @@ struct chhs_server {
             continue;
           }
         }
-        finish_locked(j, s);  // the last slice has completed, or a call failed
+        // the last slice has completed, or a call failed: out of the active
+        // set first, then torn down without the lock
         active.erase(active.begin() + q);
+        finish(lk, j, s);
         cv.notify_all();
       }
       if (progressed) continue;
@@ -381,7 +401,8 @@ void chhs_server_destroy(chhs_server_t* sv) {
   std::lock_guard<std::mutex> lk(sv->mu);
   for (Job* j : sv->active) {
     cudaStreamSynchronize(j->stream);
-    sv->finish_locked(j, CHHS_ERR_INVALID_ARG);
+    sv->teardown(j);
+    sv->record_locked(j, CHHS_ERR_INVALID_ARG);
   }
   for (auto& kv : sv->all) delete kv.second;
   sv->all.clear();

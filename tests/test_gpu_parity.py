@@ -55,6 +55,11 @@ def _check_step(run, h, eps, gamma, dt, tol_phi):
     ((2, 2), 0.5, 0.2, 1.0, 0.01),         # single level: the coarsest solve only
     ((8, 8, 8), 0.2, 0.1, 2.0, 0.01),
     ((16, 8, 12), 0.1, 0.08, 4.0, 0.005),  # 3D, uneven
+    # gamma = 0 (Section 5.2 runs it): Eq. 2.7 decouples the pressure, whose
+    # equation becomes Lap_h p = 0, and the velocity vanishes
+    ((24, 40), 0.1, 0.08, 0.0, 0.01),      # ragged
+    ((64, 32), 0.05, 0.05, 0.0, 0.01),
+    ((16, 8, 12), 0.1, 0.08, 0.0, 0.005),  # 3D, uneven
 ])
 def test_single_steps_match_oracle(shape, h, eps, gamma, dt, precision):
     phi0 = inputs.spinodal(shape, 101, mean=0.0, amplitude=0.5)
@@ -319,13 +324,24 @@ def test_largest_served_sizes_satisfy_the_scheme(case, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("eps,gamma", [(0.02, 0.5), (0.02, 4.0), (0.08, 4.0)])
-def test_served_parameter_extremes_match_oracle(eps, gamma, precision):
-    """Corners of the served parameter range (eps 0.02-0.08, gamma 0.5-4,
-    h 0.025, dt 0.005) on a 256^2 spinodal: every GPU step equals the oracle's
-    converged step within the form's tolerance."""
-    shape, h, dt = (256, 256), 0.025, 0.005
-    phi0 = inputs.spinodal(shape, 61, mean=-0.1, amplitude=0.05)
+@pytest.mark.parametrize("gamma", [0.0, 0.5, 4.0])
+@pytest.mark.parametrize("eps", [0.02, 0.08])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_served_parameter_range_matches_oracle(dim, eps, gamma, precision):
+    """The served parameter range (eps 0.02-0.08, gamma 0 and 0.5-4, dt
+    0.005; h 0.025 in 2D and 0.05 in 3D) at the solver's default settings:
+    every GPU step equals the oracle's converged step within the form's
+    tolerance.  2D: a 256^2 spinodal; 3D: tanh bubbles on 32^3 (the served 3D
+    grids share its h, so its interfaces are as thin relative to the cells:
+    eps/h = 0.4 at eps = 0.02)."""
+    dt = 0.005
+    if dim == 2:
+        shape, h = (256, 256), 0.025
+        phi0 = inputs.spinodal(shape, 61, mean=-0.1, amplitude=0.05)
+    else:
+        n, h = 32, 0.05
+        shape = (n, n, n)
+        phi0 = inputs.bubbles(n, n * h, eps, 63, count=3, rmin=0.3, rmax=0.5)
     with _run(shape, h, eps, gamma, dt, precision) as run:
         run.set_phi(phi0)
         for _ in range(2):
@@ -335,13 +351,14 @@ def test_served_parameter_extremes_match_oracle(eps, gamma, precision):
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_served_3d_extreme_matches_oracle(precision):
     """The 3D end of the served range (h 0.05, eps 0.02, gamma 4) on 64^3
-    bubbles: each GPU step equals the oracle's within the form's tolerance.
-    The interfaces are under-resolved here (eps/h = 0.4), and the RMS stop at
-    1e-10 leaves max|dphi| = 1.2e-9 in double precision; as for any such
-    case, the parity run stops the GPU at 1e-11 rather than loosen the bound."""
+    bubbles, at the default settings: each GPU step equals the oracle's
+    within the form's tolerance.  The interfaces are under-resolved here
+    (eps/h = 0.4) and the residual concentrates on them, so the mean-square
+    stop alone left max|dphi| = 1.2e-9 in double precision; the pointwise
+    guard of the default stopping rule keeps it inside the bound."""
     n, h, eps, gamma, dt = 64, 0.05, 0.02, 4.0, 0.005
     phi0 = inputs.bubbles(n, n * h, eps, 62, count=4, rmin=0.4, rmax=0.8)
-    with _run((n, n, n), h, eps, gamma, dt, precision, tol=1e-11) as run:
+    with _run((n, n, n), h, eps, gamma, dt, precision) as run:
         run.set_phi(phi0)
         for _ in range(2):
             _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
