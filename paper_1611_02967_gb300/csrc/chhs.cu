@@ -25,6 +25,7 @@
 #include "../../include/chhs.h"
 #include "chhs_kernels.cuh"
 #include "chhs_tile.cuh"
+#include "chhs_corr3.cuh"
 
 using namespace chhs_dev;
 
@@ -360,6 +361,10 @@ struct Enqueue {
       launch(run, s, CHHS_K_COARSE_RHS, L.ncell, [&] {
         pdl(k_coarse_rhs<T, DIM, CORR>, nblocks(L.ncell), kBlock, s, L, K);
       });
+    if constexpr (recompute_coefs<T, CORR>()) {
+      corr_vcycle_level(run, s, lev, tail, l);
+      return;
+    }
     smooth<T, CORR>(run, s, L, run->opts.nu1, rhs && run->opts.nu1 > 0);
     constexpr int TX = DIM == 3 ? 8 : 16;
     const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
@@ -380,11 +385,60 @@ struct Enqueue {
     smooth<T, CORR>(run, s, L, run->opts.nu2, false);
   }
 
+  // 3D single-precision (correction-form) levels above the tail: colour
+  // passes with the coefficients recomputed from phi* (k_smooth_c), the
+  // prolongation folded into the first post-smoothing sweep and, on the
+  // finest level, the update u <- u + e into the last pass.
+  template <typename T, bool CORR>
+  static constexpr bool recompute_coefs() { return DIM == 3 && std::is_same<T, float>::value && CORR; }
+
+  static void corr_vcycle_level(chhs_t* run, cudaStream_t s, const std::vector<Level<float>>& lev,
+                                const Tail<float>& tail, int l) {
+    const Coefs<float> K = coefs<float>(run);
+    const Level<float>& L = lev[l];
+    const Level<float>& C = lev[l + 1];
+    const bool rhs = l > 0;
+    const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
+    const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
+    const int kind = l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH;
+    const Level<double> none{};
+    const int nu1 = run->opts.nu1, nu2 = run->opts.nu2;
+    for (int it = 0; it < nu1; ++it)
+      for (int colour = 0; colour < 2; ++colour)
+        launch(run, s, kind, colour_cells(L, colour), [&] {
+          pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, (rhs && it == 0) ? 1 : 0, 0, none);
+        });
+    constexpr int TX = DIM == 3 ? 8 : 16;
+    const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
+    const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
+    launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
+      pdl(k_residual_restrict_c<DIM>, rblocks, kBlock, s, L, C, K);
+    });
+    vcycle<float, true>(run, s, lev, tail, l + 1);
+    if (nu2 == 0) {
+      launch(run, s, CHHS_K_PROLONG, L.ncell, [&] {
+        pdl(k_prolong<float, DIM>, nblocks(L.ncell), kBlock, s, L, C);
+      });
+      return;
+    }
+    for (int it = 0; it < nu2; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        const int pro = it == 0 ? (colour == 0 ? 1 : 2) : 0;
+        const bool upd = l == 0 && fused_update(run) && it == nu2 - 1 && colour == 1;
+        launch(run, s, kind, colour_cells(L, colour), [&] {
+          pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, 0, pro, upd ? run->lev[0] : none);
+        });
+      }
+  }
+
   static bool mixed(const chhs_t* run) { return run->opts.precision == 1; }
 
-  // Mixed form whose finest level is tiled (2D, not the tail): the last tile
-  // launch of a V-cycle performs the update u <- u + e (k_mixed_update otherwise).
-  static bool fused_update(const chhs_t* run) { return mixed(run) && DIM == 2 && run->tail_start > 0; }
+  // Mixed form whose finest level is not in the tail: the last smoothing
+  // launch of a V-cycle performs the update u <- u + e (the 2D tile, or in 3D
+  // the last colour pass when there is post-smoothing); k_mixed_update otherwise.
+  static bool fused_update(const chhs_t* run) {
+    return mixed(run) && run->tail_start > 0 && (DIM == 2 || run->opts.nu2 > 0);
+  }
 
   // The fused tile kernels serve the 2D single-precision V-cycles.
   template <typename T>
@@ -819,7 +873,7 @@ chhs_status chhs_default_opts(chhs_opts* o) {
   o->coarsest = 2;
   o->tol = 1e-10;
   o->precision = 0;
-  o->max_factor = 10.0;
+  o->max_factor = 50.0;
   return CHHS_OK;
 }
 
