@@ -323,6 +323,74 @@ chhs_status chhs_server_stats(chhs_server_t* sv, int* queued, int* active, int* 
 /* Stop the worker (runs still active are abandoned) and free everything. */
 void chhs_server_destroy(chhs_server_t* sv);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent runs of uneven size stepped together: one CUDA graph per
+ * time step of all the runs, in which every launch covers one kernel of one
+ * multigrid level for all runs that have that level (the V-cycle's level l is
+ * one launch over every run's level l; all runs' coarse tails are one launch
+ * of one block per run; all runs' stopping norms are one launch), with the
+ * V-cycle loop on the device running while any run is still iterating.  A
+ * run that has converged drops out of the launches, so each run takes
+ * exactly the V-cycles, and computes exactly the bits, that it does alone
+ * (chhs_create with the same options).  Batches use the mixed-precision form
+ * (opts->precision must be 1; NULL opts = the defaults with precision 1).
+ * The paper has no counterpart: batching is a property of this
+ * implementation. */
+typedef struct chhs_batch chhs_batch_t;
+
+/* One run of a batch: the chhs_create arguments (Section 2). */
+typedef struct {
+    int dim;      /* 2 or 3, the same for every run of a batch */
+    int n[3];     /* grid size (n[2] ignored in 2D) */
+    double h, eps, gamma, dt;
+} chhs_run_desc;
+
+/* Device bytes chhs_batch_create allocates for these runs (0 for invalid
+ * arguments: nruns < 1, a run that chhs_create would refuse, runs of
+ * different dimension, options other than the mixed-precision form). */
+size_t chhs_batch_workspace_bytes(int nruns, const chhs_run_desc* runs, const chhs_opts* opts);
+
+/* Create a batch of nruns runs (arrays: runs[nruns]) on cuda_stream (NULL =
+ * a stream the batch creates).  Allocates every run's hierarchy in one
+ * cudaMalloc and the launch tables in another, and captures the batch's
+ * step graph.  Each run starts at phi^0 = phi^{-1} = 0.  Errors:
+ * CHHS_ERR_INVALID_ARG (as chhs_batch_workspace_bytes, or a run whose
+ * coarse tail needs more shared memory than a block has), CHHS_ERR_OOM,
+ * CHHS_ERR_CUDA. */
+chhs_status chhs_batch_create(int nruns, const chhs_run_desc* runs, const chhs_opts* opts, void* cuda_stream,
+                              chhs_batch_t** out);
+
+/* Number of runs of the batch (0 for NULL). */
+int chhs_batch_size(const chhs_batch_t* batch);
+
+/* The handle of run r (0 <= r < nruns; NULL otherwise), owned by the batch.
+ * Use it with chhs_set_phi, chhs_set_state, chhs_get_phi, chhs_get_state,
+ * chhs_mass, chhs_energy, chhs_dissipation and chhs_velocity (in stream
+ * order on the batch's stream); chhs_step, chhs_step_async and
+ * chhs_autotune refuse it (CHHS_ERR_INVALID_ARG), and chhs_destroy ignores
+ * it: the batch frees it. */
+chhs_t* chhs_batch_run(chhs_batch_t* batch, int r);
+
+/* Advance every run nsteps time steps; blocks until done.  Per run (arrays
+ * of nruns, each nullable): status_out (a chhs_status: CHHS_OK, or
+ * CHHS_ERR_NOT_CONVERGED / CHHS_ERR_DIVERGED for a run that stopped at a
+ * failed step, its phi^m and phi^{m-1} then at the last accepted step, as
+ * chhs_step leaves them), vcycles_out (V-cycles summed over the steps) and
+ * resid_out (the last stopping norm).  Returns CHHS_OK if every run
+ * advanced, else the first failing run's status (chhs_batch_last_error
+ * names it); the other runs advance either way. */
+chhs_status chhs_batch_step(chhs_batch_t* batch, int nsteps, int* status_out, int* vcycles_out, double* resid_out);
+
+/* Launches of the batch's step graph: per V-cycle and per step outside the
+ * V-cycle loop, whatever the number of runs. */
+chhs_status chhs_batch_launch_counts(const chhs_batch_t* batch, int* per_vcycle, int* per_step);
+
+/* Text of the batch's last error ("" if none). */
+const char* chhs_batch_last_error(const chhs_batch_t* batch);
+
+/* Free the batch, its runs and its device memory.  NULL is a no-op. */
+void chhs_batch_destroy(chhs_batch_t* batch);
+
 /* Number of multigrid levels of the handle (finest included). */
 int chhs_num_levels(const chhs_t* run);
 

@@ -28,7 +28,8 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_num_levels", "chhs_destroy", "chhs_last_error", "chhs_energy_noalloc", "chhs_dissipation",
            "chhs_server_create", "chhs_server_submit", "chhs_server_wait", "chhs_server_result",
            "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity",
-           "chhs_autotune"]
+           "chhs_autotune", "chhs_batch_workspace_bytes", "chhs_batch_create", "chhs_batch_size", "chhs_batch_run",
+           "chhs_batch_step", "chhs_batch_launch_counts", "chhs_batch_last_error", "chhs_batch_destroy"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
@@ -44,6 +45,11 @@ class chhs_request(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("eps", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("phi0", ctypes.c_void_p), ("phi_prev", ctypes.c_void_p)]
+
+
+class chhs_run_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("eps", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -102,6 +108,14 @@ def lib():
             "chhs_destroy": (None, [_vp]),
             "chhs_last_error": (ctypes.c_char_p, [_vp]),
             "chhs_energy_noalloc": (i, [i, _ip, d, d, _vp, _vp, _vp, _dp, _dp, _dp]),
+            "chhs_batch_workspace_bytes": (sz, [i, ctypes.POINTER(chhs_run_desc), optp]),
+            "chhs_batch_create": (i, [i, ctypes.POINTER(chhs_run_desc), optp, _vp, ctypes.POINTER(_vp)]),
+            "chhs_batch_size": (i, [_vp]),
+            "chhs_batch_run": (_vp, [_vp, i]),
+            "chhs_batch_step": (i, [_vp, i, _ip, _ip, _dp]),
+            "chhs_batch_launch_counts": (i, [_vp, _ip, _ip]),
+            "chhs_batch_last_error": (ctypes.c_char_p, [_vp]),
+            "chhs_batch_destroy": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -168,6 +182,18 @@ def workspace_bytes(shape, opts=None):
 class Run:
     """One CHHS run (a chhs_t handle)."""
 
+    @classmethod
+    def _member(cls, handle, shape, h, eps, gamma, dt):
+        """A run owned by a Batch (chhs_batch_run): usable, never destroyed here."""
+        self = cls.__new__(cls)
+        self.shape = tuple(int(x) for x in shape)
+        self.ncell = int(np.prod(self.shape))
+        self.h, self.eps, self.gamma, self.dt = float(h), float(eps), float(gamma), float(dt)
+        self._arena = None
+        self.handle = ctypes.c_void_p(handle)
+        self._member_of_batch = True
+        return self
+
     def __init__(self, shape, h, eps, gamma, dt, opts=None, stream=None, arena=None):
         self.shape = tuple(int(x) for x in shape)
         self.ncell = int(np.prod(self.shape))
@@ -193,7 +219,8 @@ class Run:
 
     def close(self):
         if getattr(self, "handle", None):
-            lib().chhs_destroy(self.handle)
+            if not getattr(self, "_member_of_batch", False):
+                lib().chhs_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -383,6 +410,66 @@ class Server:
     def close(self):
         if getattr(self, "handle", None):
             lib().chhs_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many runs stepped by one graph of batched launches (chhs_batch_*).
+
+    runs: a list of (shape, h, eps, gamma, dt), all 2D or all 3D.  The
+    batch uses the mixed-precision form; opts (chhs_opts) defaults to it."""
+
+    def __init__(self, runs, opts=None, stream=None):
+        self.specs = [(tuple(int(x) for x in r[0]),) + tuple(float(v) for v in r[1:]) for r in runs]
+        descs = (chhs_run_desc * len(runs))()
+        for q, (shape, h, eps, gamma, dt) in enumerate(self.specs):
+            dim, n = _dims(shape)
+            descs[q] = chhs_run_desc(dim, n, h, eps, gamma, dt)
+        self._descs = descs
+        if opts is None:
+            opts = default_opts(precision=1)
+        h = ctypes.c_void_p()
+        st = lib().chhs_batch_create(len(runs), descs, ctypes.byref(opts), ctypes.c_void_p(stream) if stream else None,
+                                     ctypes.byref(h))
+        if st != CHHS_OK:
+            raise ChhsError(st, "chhs_batch_create failed")
+        self.handle = h
+        self.runs = [Run._member(lib().chhs_batch_run(h, q), *self.specs[q]) for q in range(len(runs))]
+
+    def __len__(self):
+        return lib().chhs_batch_size(self.handle)
+
+    def step(self, nsteps=1, check=True):
+        """Advance every run nsteps; returns (statuses, V-cycles, residuals) per run."""
+        n = len(self.runs)
+        s_, v_, r_ = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_double * n)()
+        st = lib().chhs_batch_step(self.handle, int(nsteps), s_, v_, r_)
+        if check and st != CHHS_OK:
+            raise ChhsError(st, lib().chhs_batch_last_error(self.handle).decode())
+        return list(s_), list(v_), list(r_)
+
+    def launch_counts(self):
+        a, b = ctypes.c_int(0), ctypes.c_int(0)
+        lib().chhs_batch_launch_counts(self.handle, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for r in self.runs:
+                r.handle = None
+            lib().chhs_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

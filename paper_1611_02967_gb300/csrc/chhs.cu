@@ -26,6 +26,7 @@
 #include "chhs_kernels.cuh"
 #include "chhs_tile.cuh"
 #include "chhs_corr3.cuh"
+#include "chhs_batch.cuh"
 
 using namespace chhs_dev;
 
@@ -191,11 +192,14 @@ struct chhs {
   bool pending = false;  // steps enqueued by chhs_step_async since the last chhs_wait
   int* counter = nullptr;  // counts launches while the graph is captured
   Prof* prof = nullptr;  // per-launch events while profiling
+  bool batch_member = false;  // a run of a chhs_batch: stepped by the batch's graph, freed by the batch
   std::string err;
   int ncell() const { return n[0] * n[1] * n[2]; }
 };
 
 namespace {
+
+void destroy_handle(chhs_t* run);
 
 chhs_status fail(chhs_t* r, chhs_status s, const std::string& msg) {
   if (r) r->err = msg;
@@ -789,6 +793,7 @@ chhs_status setup_handle(chhs_t* run) {
   CU(cudaMemsetAsync(run->arena, 0, Lo.total, run->stream));
   CU(cudaMallocHost(&run->host_st, sizeof(DevState)));
   memset(run->host_st, 0, sizeof(DevState));
+  if (run->batch_member) return CHHS_OK;  // the batch builds the one graph of all its runs
   chhs_status s = run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
   if (s != CHHS_OK) return s;
   CU(cudaStreamSynchronize(run->stream));
@@ -797,7 +802,7 @@ chhs_status setup_handle(chhs_t* run) {
 
 chhs_status create_impl(int dim, const int n[3], double h, double eps, double gamma, double dt,
                         const chhs_opts* opts, void* cuda_stream, void* arena, size_t arena_bytes,
-                        chhs_t** out) {
+                        chhs_t** out, bool member = false) {
   if (!out) return CHHS_ERR_INVALID_ARG;
   *out = nullptr;
   chhs_opts o;
@@ -817,6 +822,7 @@ chhs_status create_impl(int dim, const int n[3], double h, double eps, double ga
   run->h = h; run->eps = eps; run->gamma = gamma; run->dt = dt;
   run->opts = o;
   run->layout = std::move(layout);
+  run->batch_member = member;
   chhs_status s = CHHS_OK;
   if (cuda_stream) {
     run->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -833,14 +839,14 @@ chhs_status create_impl(int dim, const int n[3], double h, double eps, double ga
     if (cudaMalloc(&run->arena, run->layout.total) != cudaSuccess) {
       cudaGetLastError();
       run->arena = nullptr;
-      chhs_destroy(run);
+      destroy_handle(run);
       return CHHS_ERR_OOM;
     }
     run->own_arena = true;
   }
   s = setup_handle(run);
   if (s != CHHS_OK) {
-    chhs_destroy(run);
+    destroy_handle(run);
     return s;
   }
   *out = run;
@@ -930,6 +936,7 @@ chhs_status chhs_set_state(chhs_t* run, const double* phi, const double* phi_pre
 
 chhs_status chhs_step_async(chhs_t* run, int nsteps) {
   if (!run) return CHHS_ERR_INVALID_ARG;
+  if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch is stepped by chhs_batch_step");
   if (nsteps < 0) return fail(run, CHHS_ERR_INVALID_ARG, "nsteps < 0");
   run->err.clear();
   if (!run->pending) {  // the first call since the last wait starts a new count
@@ -1042,6 +1049,7 @@ chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass) {
 
 chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   if (!run || trial_steps < 1) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
+  if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   run->err.clear();
   struct Cand {
@@ -1218,7 +1226,15 @@ chhs_status chhs_get_state(chhs_t* run, double* phi, double* phi_prev, double* m
 int chhs_num_levels(const chhs_t* run) { return run ? (int)run->lev.size() : 0; }
 
 void chhs_destroy(chhs_t* run) {
-  if (!run) return;
+  if (!run || run->batch_member) return;  // a batch's runs are released with the batch
+  destroy_handle(run);
+}
+
+}  // extern "C"
+
+namespace {
+
+void destroy_handle(chhs_t* run) {
   if (run->stream) cudaStreamSynchronize(run->stream);
   if (run->exec) cudaGraphExecDestroy(run->exec);
   if (run->graph) cudaGraphDestroy(run->graph);
@@ -1228,6 +1244,575 @@ void chhs_destroy(chhs_t* run) {
   delete run;
 }
 
-const char* chhs_last_error(const chhs_t* run) { return run ? run->err.c_str() : "NULL handle"; }
+}  // namespace
+
+extern "C" const char* chhs_last_error(const chhs_t* run) { return run ? run->err.c_str() : "NULL handle"; }
+
+// ------------------------------------------------------------------ batches
+//
+// chhs_batch_*: many independent runs of the mixed-precision form stepped by
+// one CUDA graph.  Each launch of the graph covers one kernel of one
+// multigrid level for every run that has that level (chhs_batch.cuh): level
+// l of the V-cycle is one launch over all runs' level l, all runs' coarse
+// tails are one launch of one block per run, and the stopping norms of all
+// runs are one launch whose last block keeps the loop going while any run is
+// still iterating.  Runs that have converged drop out of the launches (their
+// blocks return at once), so each run takes exactly the V-cycles it takes
+// alone, and the per-run work is the same device code with the same block
+// shapes as its own graph: a run's results are bit-identical to a solo run
+// with the same options.
+
+struct chhs_batch {
+  int dim = 2, nruns = 0;
+  chhs_opts opts{};
+  std::vector<chhs_t*> runs;
+  char* arena = nullptr;            // every run's hierarchy
+  char* tables = nullptr;           // job tables of the batched launches
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevState** d_sts = nullptr;       // per run, for the reset and gather kernels
+  unsigned int* d_ticket = nullptr; // blocks of a batched norm launch that have finished
+  int* d_out = nullptr;             // status[n], vcycles[n], then resid[n] (doubles)
+  char* h_out = nullptr;            // pinned mirror of d_out
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches_per_v = 0, launches_per_step = 0;
+  std::string err;
+};
+
+namespace {
+
+chhs_status bfail(chhs_batch_t* b, chhs_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+#define BCU(call)                                                                           \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return bfail(b, CHHS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+// Jobs of one batched launch and the prefix sum of their block counts.
+template <class J>
+struct JobList {
+  std::vector<J> jobs;
+  std::vector<int> start{0};
+  void add(const J& j, int blocks) {
+    jobs.push_back(j);
+    start.push_back(start.back() + blocks);
+  }
+  int njobs() const { return (int)jobs.size(); }
+  int blocks() const { return start.back(); }
+};
+
+// The batch's step, written once and walked twice: first to lay out the job
+// tables (plan), then to launch into the capture stream with the tables'
+// device addresses (capture), in the same order.
+template <int DIM>
+struct BatchStep {
+  chhs_batch_t* b;
+  bool capture = false;
+  std::vector<char> buf;            // host image of the job tables
+  std::vector<size_t> offs;         // table offsets in emission order
+  size_t cur = 0;
+  int* counter = nullptr;           // launches, while capturing
+  size_t tile_smem = 0, tail_smem = 0;
+
+  size_t put(const void* p, size_t n) {
+    const size_t off = align_up(buf.size());
+    buf.resize(off + n);
+    if (n) memcpy(buf.data() + off, p, n);
+    return off;
+  }
+
+  // Launch one batched kernel (or, when planning, lay out its tables).
+  template <class J, typename... KArgs, typename... Args>
+  void go(const JobList<J>& jl, void (*kernel)(KArgs...), int block, size_t smem, cudaStream_t s, Args... extra) {
+    if (jl.jobs.empty()) return;
+    if (!capture) {
+      offs.push_back(put(jl.jobs.data(), sizeof(J) * jl.jobs.size()));
+      offs.push_back(put(jl.start.data(), sizeof(int) * jl.start.size()));
+      return;
+    }
+    const J* dj = reinterpret_cast<const J*>(b->tables + offs[cur++]);
+    const int* ds = reinterpret_cast<const int*>(b->tables + offs[cur++]);
+    if (counter) ++*counter;
+    pdl_smem(kernel, jl.blocks(), block, smem, s, dj, ds, jl.njobs(), extra...);
+  }
+
+  // The tail launch: one block per job, no prefix sum.
+  void go_tail(const std::vector<TailJob<float>>& jobs, cudaStream_t s) {
+    if (jobs.empty()) return;
+    if (!capture) {
+      offs.push_back(put(jobs.data(), sizeof(TailJob<float>) * jobs.size()));
+      return;
+    }
+    const TailJob<float>* dj = reinterpret_cast<const TailJob<float>*>(b->tables + offs[cur++]);
+    if (counter) ++*counter;
+    pdl_smem(kb_tail<float, DIM, true>, (int)jobs.size(), kTailThreads, tail_smem, s, dj);
+  }
+
+  static Coefs<float> k32(const chhs_t* r) { return Enqueue<DIM>::template coefs<float>(r); }
+  static Coefs<double> k64(const chhs_t* r) { return Enqueue<DIM>::template coefs<double>(r); }
+
+  int max_tail_start() const {
+    int m = 0;
+    for (const chhs_t* r : b->runs) m = std::max(m, r->tail_start);
+    return m;
+  }
+
+  void setup(cudaStream_t s) {
+    JobList<SetupJob> jl;
+    for (chhs_t* r : b->runs) {
+      const Level<double>& F = r->lev[0];
+      jl.add(SetupJob{F, F, r->phimm1, r->eps * r->eps, r->st, k64(r), 0}, nblocks(F.ncell));
+    }
+    go(jl, kb_setup_coef<DIM>, kBlock, 0, s);
+  }
+
+  void coefs(cudaStream_t s) {
+    JobList<CoefF32Job> jf;
+    int maxng = 0;
+    for (chhs_t* r : b->runs) {
+      const int ng = (int)r->lev32.size();
+      maxng = std::max(maxng, ng);
+      jf.add(CoefF32Job{r->lev[0], r->lev32[0], ng > 1 ? r->lev32[1] : r->lev32[0], k32(r), ng > 1 ? 1 : 0},
+             nblocks(r->lev[0].ncell));
+    }
+    go(jf, kb_coef_restrict_f32<DIM>, kBlock, 0, s);
+    for (int l = 1; l < maxng; ++l) {
+      JobList<CoefJob> jl;
+      for (chhs_t* r : b->runs) {
+        const int ng = (int)r->lev32.size();
+        if (l >= ng) continue;
+        const Level<float>& G = r->lev32[l];
+        jl.add(CoefJob{G, l + 1 < ng ? r->lev32[l + 1] : G, k32(r), l + 1 < ng ? 1 : 0}, nblocks(G.ncell));
+      }
+      go(jl, kb_coef_restrict<DIM>, kBlock, 0, s);
+    }
+  }
+
+  void norm(cudaStream_t s, cudaGraphConditionalHandle cond, int mode) {
+    JobList<NormJob> jl;
+    for (chhs_t* r : b->runs)
+      jl.add(NormJob{r->lev[0], r->lev32[0], k64(r), r->partials, r->st}, r->norm_blocks);
+    go(jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cond, mode);
+  }
+
+  void vcycle(cudaStream_t s) {
+    const int ts = max_tail_start();
+    const int nu1 = b->opts.nu1, nu2 = b->opts.nu2;
+    for (int l = 0; l < ts; ++l) pre(s, l, nu1);
+    std::vector<TailJob<float>> tails;
+    for (chhs_t* r : b->runs) tails.push_back(TailJob<float>{r->tail32, k32(r), r->st});
+    go_tail(tails, s);
+    for (int l = ts - 1; l >= 0; --l) post(s, l, nu2);
+    JobList<PairJob> upd;
+    for (chhs_t* r : b->runs)
+      if (!Enqueue<DIM>::fused_update(r))
+        upd.add(PairJob{r->lev32[0], r->lev32[0], k32(r), r->lev[0], r->st}, nblocks(r->lev[0].ncell));
+    go(upd, kb_mixed_update, kBlock, 0, s);
+  }
+
+  void pre(cudaStream_t s, int l, int nu1) {
+    if (DIM == 2) {
+      JobList<TileJob<float>> jl;
+      const int np1 = 2 * nu1;
+      for (chhs_t* r : b->runs) {
+        if (l >= r->tail_start) continue;
+        const Level<float>& L = r->lev32[l];
+        const TileOut<float> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3, nullptr, nullptr, nullptr};
+        const int gx = (L.nx + kTileW - 1) / kTileW, gy = (L.ny + kTileH - 1) / kTileH;
+        jl.add(TileJob<float>{L, r->lev32[l + 1], k32(r), to_copy, r->st, np1, np1 + 1, l > 0 ? 1 : 0, 0, 1, gx},
+               gx * gy);
+      }
+      go(jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
+      return;
+    }
+    auto runs_at = [&](auto add) {
+      for (chhs_t* r : b->runs)
+        if (l < r->tail_start) add(r, r->lev32[l], r->lev32[l + 1]);
+    };
+    if (l > 0 && nu1 == 0) {
+      JobList<PairJob> jl;
+      runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
+        jl.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, nblocks(L.ncell));
+      });
+      go(jl, kb_coarse_rhs<DIM>, kBlock, 0, s);
+    }
+    for (int it = 0; it < nu1; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        JobList<SmoothCJob> jl;
+        runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
+          const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
+          jl.add(SmoothCJob{L, C, Level<double>{}, k32(r), r->st, colour, (l > 0 && it == 0) ? 1 : 0, 0},
+                 (threads + kSmoothBlock - 1) / kSmoothBlock);
+        });
+        go(jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
+      }
+    JobList<PairJob> jr;
+    runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
+      constexpr int TX = DIM == 3 ? 8 : 16;
+      const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
+      jr.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, (int)((tiles * 32 + kBlock - 1) / kBlock));
+    });
+    go(jr, kb_residual_restrict_c<DIM>, kBlock, 0, s);
+  }
+
+  void post(cudaStream_t s, int l, int nu2) {
+    if (DIM == 2) {
+      JobList<TileJob<float>> jl;
+      const int np2 = 2 * nu2;
+      for (chhs_t* r : b->runs) {
+        if (l >= r->tail_start) continue;
+        const Level<float>& L = r->lev32[l];
+        Level<float> Lb = L;
+        Lb.phi = L.phi2;
+        Lb.mu = L.mu2;
+        Lb.p = L.p2;
+        if (l > 0) {
+          Lb.fphi = L.fc1;
+          Lb.fmu = L.fc2;
+          Lb.fp = L.fc3;
+        }
+        TileOut<float> to_state{L.phi, L.mu, L.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        if (l == 0 && Enqueue<DIM>::fused_update(r)) {
+          to_state.phi64 = r->lev[0].phi;
+          to_state.mu64 = r->lev[0].mu;
+          to_state.p64 = r->lev[0].p;
+        }
+        const int gx = (L.nx + kTileW - 1) / kTileW, gy = (L.ny + kTileH - 1) / kTileH;
+        jl.add(TileJob<float>{Lb, r->lev32[l + 1], k32(r), to_state, r->st, np2, np2, 0, 1, 0, gx}, gx * gy);
+      }
+      go(jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
+      return;
+    }
+    auto runs_at = [&](auto add) {
+      for (chhs_t* r : b->runs)
+        if (l < r->tail_start) add(r, r->lev32[l], r->lev32[l + 1]);
+    };
+    if (nu2 == 0) {
+      JobList<PairJob> jl;
+      runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
+        jl.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, nblocks(L.ncell));
+      });
+      go(jl, kb_prolong<DIM>, kBlock, 0, s);
+      return;
+    }
+    for (int it = 0; it < nu2; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        JobList<SmoothCJob> jl;
+        const int pro = it == 0 ? (colour == 0 ? 1 : 2) : 0;
+        runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
+          const bool upd = l == 0 && Enqueue<DIM>::fused_update(r) && it == nu2 - 1 && colour == 1;
+          const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
+          jl.add(SmoothCJob{L, C, upd ? r->lev[0] : Level<double>{}, k32(r), r->st, colour, 0, pro},
+                 (threads + kSmoothBlock - 1) / kSmoothBlock);
+        });
+        go(jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
+      }
+  }
+
+  void advance(cudaStream_t s) {
+    JobList<AdvanceJob> jl;
+    for (chhs_t* r : b->runs) jl.add(AdvanceJob{r->lev[0], r->phimm1, r->st}, nblocks(r->lev[0].ncell));
+    go(jl, kb_advance, kBlock, 0, s);
+  }
+
+  // Plan: lay out every table in emission order (no CUDA calls).
+  void plan() {
+    capture = false;
+    setup(nullptr);
+    coefs(nullptr);
+    norm(nullptr, 0, 0);
+    vcycle(nullptr);
+    norm(nullptr, 0, 1);
+    advance(nullptr);
+  }
+
+  // Shared memory of the batched tile and tail launches, opted in (only ever raised).
+  chhs_status prepare() {
+    int dev = 0, optin = 0;
+    BCU(cudaGetDevice(&dev));
+    BCU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (chhs_t* r : b->runs) tail_smem = std::max(tail_smem, Enqueue<DIM>::template tail_bytes<float, true>(r->tail32));
+    if (DIM == 2) {
+      const int halo = 2 * std::max(b->opts.nu1, b->opts.nu2) + 1;
+      tile_smem = tile_smem_bytes(halo, tile_nfields<true>(), sizeof(float));
+    }
+    auto raise_to = [&](const void* fn, size_t dyn) -> chhs_status {
+      cudaFuncAttributes fa;
+      BCU(cudaFuncGetAttributes(&fa, fn));
+      if (dyn + fa.sharedSizeBytes > (size_t)optin)
+        return bfail(b, CHHS_ERR_INVALID_ARG, "a run's coarse tail or tiles need more shared memory than a block has");
+      if ((size_t)fa.maxDynamicSharedSizeBytes < dyn)
+        BCU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      return CHHS_OK;
+    };
+    chhs_status st = raise_to(reinterpret_cast<const void*>(kb_tail<float, DIM, true>), tail_smem);
+    if (st != CHHS_OK) return st;
+    if (DIM == 2) {
+      st = raise_to(reinterpret_cast<const void*>(kb_tile<float, true>), tile_smem);
+      if (st != CHHS_OK) return st;
+    }
+    return CHHS_OK;
+  }
+
+  // Capture the step graph (the structure of a single run's build_graph).
+  chhs_status build() {
+    chhs_status ps = prepare();
+    if (ps != CHHS_OK) return ps;
+    plan();
+    BCU(cudaMalloc(&b->tables, std::max<size_t>(buf.size(), 256)));
+    BCU(cudaMemcpy(b->tables, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    capture = true;
+    cur = 0;
+    struct CaptureRes {
+      cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~CaptureRes() {
+        for (int q : {1, 0}) {
+          cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+          if (s[q] && cudaStreamIsCapturing(s[q], &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s[q], &g);
+            if (q == 0 && g) cudaGraphDestroy(g);
+          }
+        }
+        for (cudaEvent_t ev : e)
+          if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t st : s)
+          if (st) cudaStreamDestroy(st);
+        cudaGetLastError();
+      }
+    } res;
+    for (int q = 0; q < 3; ++q) BCU(cudaStreamCreateWithFlags(&res.s[q], cudaStreamNonBlocking));
+    for (int q = 0; q < 2; ++q) BCU(cudaEventCreateWithFlags(&res.e[q], cudaEventDisableTiming));
+    cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2];
+    int n_frame = 0, n_v = 0;
+    BCU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    counter = &n_frame;
+    setup(cs);
+    BCU(cudaEventRecord(res.e[0], cs));
+    BCU(cudaStreamWaitEvent(cs3, res.e[0], 0));
+    coefs(cs3);
+    BCU(cudaEventRecord(res.e[1], cs3));
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cst;
+    BCU(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle cond;
+    BCU(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+    norm(cs, cond, 0);
+    BCU(cudaStreamWaitEvent(cs, res.e[1], 0));
+    BCU(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    BCU(cudaGraphAddNode(&loop, g, deps, nullptr, ndeps, &cp));
+    BCU(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    BCU(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    counter = &n_v;
+    vcycle(cs2);
+    norm(cs2, cond, 1);
+    BCU(cudaStreamEndCapture(cs2, &body));
+    counter = &n_frame;
+    advance(cs);
+    counter = nullptr;
+    BCU(cudaStreamEndCapture(cs, &b->graph));
+    BCU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->launches_per_v = n_v;
+    b->launches_per_step = n_frame;
+    return CHHS_OK;
+  }
+};
+
+void batch_free(chhs_batch_t* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (chhs_t* r : b->runs) destroy_handle(r);
+  if (b->tables) cudaFree(b->tables);
+  if (b->arena) cudaFree(b->arena);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Bytes of the batch's own bookkeeping after the runs' hierarchies.
+size_t batch_misc_bytes(int nruns) {
+  return align_up(sizeof(DevState*) * nruns) + align_up(sizeof(unsigned int)) +
+         align_up((2 * sizeof(int) + sizeof(double)) * nruns);
+}
+
+bool batch_args_ok(int nruns, const chhs_run_desc* runs, const chhs_opts& o) {
+  if (nruns < 1 || !runs || !valid_opts(o) || o.precision != 1) return false;
+  for (int r = 0; r < nruns; ++r) {
+    const chhs_run_desc& d = runs[r];
+    if (d.dim != runs[0].dim || !valid_problem(d.dim, d.n, d.h, d.eps, d.gamma, d.dt)) return false;
+  }
+  return true;
+}
+
+size_t batch_bytes(int nruns, const chhs_run_desc* runs, const chhs_opts& o, std::vector<size_t>* offs) {
+  size_t total = 0;
+  for (int r = 0; r < nruns; ++r) {
+    const int nn[3] = {runs[r].n[0], runs[r].n[1], runs[r].dim == 3 ? runs[r].n[2] : 1};
+    if (offs) offs->push_back(total);
+    total += align_up(make_layout(runs[r].dim, nn, o.coarsest, o.precision).total);
+  }
+  return total + batch_misc_bytes(nruns);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t chhs_batch_workspace_bytes(int nruns, const chhs_run_desc* runs, const chhs_opts* opts) {
+  chhs_opts o;
+  chhs_default_opts(&o);
+  o.precision = 1;
+  if (opts) o = *opts;
+  if (!batch_args_ok(nruns, runs, o)) return 0;
+  return batch_bytes(nruns, runs, o, nullptr);
+}
+
+chhs_status chhs_batch_create(int nruns, const chhs_run_desc* runs, const chhs_opts* opts, void* cuda_stream,
+                              chhs_batch_t** out) {
+  if (!out) return CHHS_ERR_INVALID_ARG;
+  *out = nullptr;
+  chhs_opts o;
+  chhs_default_opts(&o);
+  o.precision = 1;
+  if (opts) o = *opts;
+  if (!batch_args_ok(nruns, runs, o)) return CHHS_ERR_INVALID_ARG;
+  chhs_batch_t* b = new (std::nothrow) chhs_batch_t();
+  if (!b) return CHHS_ERR_OOM;
+  b->dim = runs[0].dim;
+  b->nruns = nruns;
+  b->opts = o;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return CHHS_ERR_CUDA;
+  } else {
+    b->own_stream = true;
+  }
+  std::vector<size_t> offs;
+  const size_t total = batch_bytes(nruns, runs, o, &offs);
+  if (cudaMalloc(&b->arena, total) != cudaSuccess) {
+    cudaGetLastError();
+    b->arena = nullptr;
+    batch_free(b);
+    return CHHS_ERR_OOM;
+  }
+  for (int r = 0; r < nruns; ++r) {
+    const chhs_run_desc& d = runs[r];
+    chhs_t* run = nullptr;
+    const int nn[3] = {d.n[0], d.n[1], d.dim == 3 ? d.n[2] : 1};
+    const size_t need = align_up(make_layout(d.dim, nn, o.coarsest, o.precision).total);
+    chhs_status s = create_impl(d.dim, d.n, d.h, d.eps, d.gamma, d.dt, &o, b->stream, b->arena + offs[r], need, &run,
+                                true);
+    if (s != CHHS_OK) {
+      batch_free(b);
+      return s;
+    }
+    b->runs.push_back(run);
+  }
+  char* misc = b->arena + (total - batch_misc_bytes(nruns));
+  b->d_sts = reinterpret_cast<DevState**>(misc);
+  misc += align_up(sizeof(DevState*) * nruns);
+  b->d_ticket = reinterpret_cast<unsigned int*>(misc);
+  misc += align_up(sizeof(unsigned int));
+  b->d_out = reinterpret_cast<int*>(misc);
+  std::vector<DevState*> sts;
+  for (chhs_t* r : b->runs) sts.push_back(r->st);
+  chhs_status s = CHHS_OK;
+  const size_t out_bytes = (2 * sizeof(int) + sizeof(double)) * nruns;
+  if (cudaMemcpy(b->d_sts, sts.data(), sizeof(DevState*) * nruns, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->d_ticket, 0, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMallocHost(&b->h_out, out_bytes) != cudaSuccess)
+    s = CHHS_ERR_CUDA;
+  if (s == CHHS_OK) {
+    if (b->dim == 2) {
+      BatchStep<2> bs{b};
+      s = bs.build();
+    } else {
+      BatchStep<3> bs{b};
+      s = bs.build();
+    }
+  }
+  if (s == CHHS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) s = CHHS_ERR_CUDA;
+  if (s != CHHS_OK) {
+    cudaGetLastError();
+    batch_free(b);
+    return s;
+  }
+  *out = b;
+  return CHHS_OK;
+}
+
+int chhs_batch_size(const chhs_batch_t* b) { return b ? b->nruns : 0; }
+
+chhs_t* chhs_batch_run(chhs_batch_t* b, int r) {
+  if (!b || r < 0 || r >= b->nruns) return nullptr;
+  return b->runs[r];
+}
+
+chhs_status chhs_batch_step(chhs_batch_t* b, int nsteps, int* status_out, int* vcycles_out, double* resid_out) {
+  if (!b) return CHHS_ERR_INVALID_ARG;
+  if (nsteps < 0) return bfail(b, CHHS_ERR_INVALID_ARG, "nsteps < 0");
+  b->err.clear();
+  const int n = b->nruns;
+  const double tol_max = tol_max_of(b->opts);
+  kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max, b->opts.max_v);
+  BCU(cudaGetLastError());
+  for (int k = 0; k < nsteps; ++k) BCU(cudaGraphLaunch(b->exec, b->stream));
+  int* d_status = b->d_out;
+  int* d_v = d_status + n;
+  double* d_res = reinterpret_cast<double*>(reinterpret_cast<char*>(b->d_out) + 2 * sizeof(int) * n);
+  kb_gather<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, d_status, d_v, d_res);
+  BCU(cudaGetLastError());
+  const size_t out_bytes = (2 * sizeof(int) + sizeof(double)) * n;
+  BCU(cudaMemcpyAsync(b->h_out, b->d_out, out_bytes, cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  const int* hs = reinterpret_cast<const int*>(b->h_out);
+  const int* hv = hs + n;
+  const double* hr = reinterpret_cast<const double*>(b->h_out + 2 * sizeof(int) * n);
+  chhs_status worst = CHHS_OK;
+  for (int r = 0; r < n; ++r) {
+    if (status_out) status_out[r] = hs[r];
+    if (vcycles_out) vcycles_out[r] = hv[r];
+    if (resid_out) resid_out[r] = hr[r];
+    if (hs[r] != 0 && worst == CHHS_OK) {
+      worst = (chhs_status)hs[r];
+      char m[96];
+      snprintf(m, sizeof m, "run %d: %s (residual %.3e)", r,
+               hs[r] == CHHS_ERR_NOT_CONVERGED ? "not converged" : "diverged", hr[r]);
+      b->err = m;
+    }
+  }
+  return worst;
+}
+
+chhs_status chhs_batch_launch_counts(const chhs_batch_t* b, int* per_vcycle, int* per_step) {
+  if (!b || !per_vcycle || !per_step) return CHHS_ERR_INVALID_ARG;
+  *per_vcycle = b->launches_per_v;
+  *per_step = b->launches_per_step;
+  return CHHS_OK;
+}
+
+const char* chhs_batch_last_error(const chhs_batch_t* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+void chhs_batch_destroy(chhs_batch_t* b) { batch_free(b); }
 
 }  // extern "C"

@@ -1,0 +1,261 @@
+// chhs_batch.cuh -- batched launches of the mixed-precision step kernels:
+// one launch runs one kernel for many independent runs of uneven size.
+//
+// Every batched kernel takes a table of jobs (one per run that takes part:
+// the arguments the run's own launch would get) and a prefix sum of the
+// jobs' block counts; block b of the launch serves job j with
+// start[j] <= b < start[j+1] as its block b - start[j].  The work of a block
+// is the same device function, with the same arguments and block index, as
+// in the run's own graph, so a run computes bit for bit what it computes
+// alone.  A job whose run has stopped iterating (converged, or failed) is
+// skipped by its blocks (gate: the run's loop flag).
+#pragma once
+#include "chhs_corr3.cuh"
+#include "chhs_kernels.cuh"
+#include "chhs_tile.cuh"
+
+namespace chhs_dev {
+
+// The job of block b: the last j with start[j] <= b (jobs without blocks
+// share their start with the next job and are never chosen).
+__device__ __forceinline__ int job_of(const int* start, int njobs, int b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// A run still iterating in the V-cycle loop (its norm kernel set go).
+__device__ __forceinline__ bool gate_open(const DevState* gate) {
+  return gate == nullptr || *(volatile const int*)&gate->go != 0;
+}
+
+struct SetupJob {
+  Level<double> L, Cn;
+  const double* phimm1;
+  double eps2;
+  const DevState* st;
+  Coefs<double> K;
+  int has_next;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_setup_coef(const SetupJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const SetupJob& J = jobs[j];
+  setup_coef_body<DIM>(blockIdx.x - start[j], J.L, J.phimm1, J.eps2, J.st, J.K, J.Cn, J.has_next);
+}
+
+struct CoefF32Job {
+  Level<double> F;
+  Level<float> G, Gn;
+  Coefs<float> K;
+  int has_next;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_coef_restrict_f32(const CoefF32Job* jobs, const int* start,
+                                                               int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const CoefF32Job& J = jobs[j];
+  coef_restrict_f32_body<DIM>(blockIdx.x - start[j], J.F, J.G, J.K, J.Gn, J.has_next);
+}
+
+struct CoefJob {
+  Level<float> L, Cn;
+  Coefs<float> K;
+  int has_next;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_coef_restrict(const CoefJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const CoefJob& J = jobs[j];
+  coef_restrict_body<float, DIM>(blockIdx.x - start[j], J.L, J.K, J.Cn, J.has_next);
+}
+
+struct NormJob {
+  Level<double> L;
+  Level<float> G;
+  Coefs<double> K;
+  double* partials;
+  DevState* st;
+};
+
+// The stopping norms of all runs (mode 0: start of a step, every run; mode 1:
+// after a V-cycle, the runs still iterating).  Each run's last block takes
+// that run's decision; the last block of the launch then sets the loop
+// condition to "any run still iterating".
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, const int* start, int njobs,
+                                                        unsigned int* ticket, cudaGraphConditionalHandle cond,
+                                                        int mode) {
+  pdl_enter();
+  __shared__ bool last_all;
+  __shared__ int any_go;
+  const int j = job_of(start, njobs, blockIdx.x);
+  const NormJob& J = jobs[j];
+  if (mode == 0 || gate_open(J.st))
+    norm_mixed_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode,
+                         0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_all = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    any_go = 0;
+  }
+  __syncthreads();
+  if (!last_all) return;
+  __threadfence();
+  int go = 0;
+  for (int q = threadIdx.x; q < njobs; q += blockDim.x) go |= __ldcg(&jobs[q].st->go);
+  if (go) any_go = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    cudaGraphSetConditional(cond, any_go ? 1u : 0u);
+  }
+}
+
+template <typename T>
+struct TileJob {
+  Level<T> L, C;
+  Coefs<T> K;
+  TileOut<T> out;
+  const DevState* gate;
+  int npass, halo, rhs, prolong, restrict_out;
+  int gx;  // tiles per row of the level
+};
+
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(kTileThreads, 2) kb_tile(const TileJob<T>* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const TileJob<T>& J = jobs[j];
+  if (!gate_open(J.gate)) return;
+  const int lb = blockIdx.x - start[j];
+  const int by = lb / J.gx, bx = lb - by * J.gx;
+  tile_body<T, CORR>(bx, by, J.L, J.C, J.K, J.npass, J.halo, J.rhs, J.prolong, J.restrict_out, J.out);
+}
+
+template <typename T>
+struct TailJob {
+  Tail<T> tl;
+  Coefs<T> K;
+  const DevState* gate;
+};
+
+// One block per job.
+template <typename T, int DIM, bool CORR>
+__global__ void __launch_bounds__(kTailThreads, 1) kb_tail(const TailJob<T>* jobs) {
+  pdl_enter();
+  const TailJob<T>& J = jobs[blockIdx.x];
+  if (!gate_open(J.gate)) return;
+  tail_body<T, DIM, CORR>(J.tl, J.K);
+}
+
+struct SmoothCJob {
+  Level<float> L, C;
+  Level<double> U;
+  Coefs<float> K;
+  const DevState* gate;
+  int colour, rhs, pro;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kSmoothBlock, 6) kb_smooth_c(const SmoothCJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const SmoothCJob& J = jobs[j];
+  if (!gate_open(J.gate)) return;
+  smooth_c_body<DIM>(blockIdx.x - start[j], J.L, J.C, J.K, J.colour, J.rhs, J.pro, J.U);
+}
+
+// Two-level jobs (residual-restriction, prolongation, coarse right-hand side)
+// and the double-precision update.
+struct PairJob {
+  Level<float> F, C;
+  Coefs<float> K;
+  Level<double> U;
+  const DevState* gate;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_residual_restrict_c(const PairJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const PairJob& J = jobs[j];
+  if (!gate_open(J.gate)) return;
+  residual_restrict_c_body<DIM>(blockIdx.x - start[j], J.F, J.C, J.K);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_prolong(const PairJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const PairJob& J = jobs[j];
+  if (!gate_open(J.gate)) return;
+  prolong_body<float, DIM>(blockIdx.x - start[j], J.F, J.C);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_coarse_rhs(const PairJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const PairJob& J = jobs[j];
+  if (!gate_open(J.gate)) return;
+  coarse_rhs_body<float, DIM, true>(blockIdx.x - start[j], J.F, J.K);
+}
+
+static __global__ void __launch_bounds__(kBlock) kb_mixed_update(const PairJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const PairJob& J = jobs[j];
+  if (!gate_open(J.gate)) return;
+  mixed_update_body(blockIdx.x - start[j], J.U, J.F);
+}
+
+struct AdvanceJob {
+  Level<double> L;
+  double* phimm1;
+  DevState* st;
+};
+
+static __global__ void __launch_bounds__(kBlock) kb_advance(const AdvanceJob* jobs, const int* start, int njobs) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const AdvanceJob& J = jobs[j];
+  advance_body(blockIdx.x - start[j], J.L, J.phimm1, J.st);
+}
+
+// The start of a batched call: every run's counters reset (one thread per run).
+static __global__ void kb_reset(DevState* const* sts, int nruns, double tol, double tol_max, int max_v) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  DevState* st = sts[r];
+  st->failed = 0;
+  st->vtotal = 0;
+  st->steps_done = 0;
+  st->tol = tol;
+  st->tol_max = tol_max;
+  st->max_v = max_v;
+}
+
+// Every run's outcome of a call: status, V-cycles (as chhs_wait reports
+// them) and the last stopping norm, gathered for one copy to the host.
+static __global__ void kb_gather(DevState* const* sts, int nruns, int* status, int* vcycles, double* resid) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  const DevState* st = sts[r];
+  status[r] = st->failed;
+  vcycles[r] = st->vtotal + (st->failed ? st->vcycles : 0);
+  resid[r] = st->resid;
+}
+
+}  // namespace chhs_dev

@@ -126,11 +126,10 @@ __device__ __forceinline__ void n_corr(const Level<float>& L, const Coefs<float>
 //        form), u <- u + e in double precision for the pass's cell and for
 //        its x-neighbour of the other colour.
 template <int DIM>
-__global__ void __launch_bounds__(kSmoothBlock) k_smooth_c(Level<float> L, Level<float> C, Coefs<float> K,
+__device__ __forceinline__ void smooth_c_body(int bx, Level<float> L, Level<float> C, Coefs<float> K,
                                                            int colour, int rhs, int pro, Level<double> U) {
-  pdl_enter();
   const int hw = (L.nx + 1) >> 1;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = bx * blockDim.x + threadIdx.x;
   int row, k;
   if (t < (1 << 21)) {
     row = small_div(t, L.rhw);
@@ -201,16 +200,22 @@ __global__ void __launch_bounds__(kSmoothBlock) k_smooth_c(Level<float> L, Level
   }
 }
 
+template <int DIM>
+__global__ void __launch_bounds__(kSmoothBlock) k_smooth_c(Level<float> L, Level<float> C, Coefs<float> K,
+                                                           int colour, int rhs, int pro, Level<double> U) {
+  pdl_enter();
+  smooth_c_body<DIM>(blockIdx.x, L, C, K, colour, rhs, pro, U);
+}
+
 // Residual of the correction form and its restriction (k_residual_restrict's
 // warp tiles of 16 x 2 / 8 x 2 x 2 fine cells, children summed by shuffles),
 // with recomputed coefficients.  Writes u_c = u_c^0 = R e, f_c = R r and
 // phi_b,c = R phi_b.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_residual_restrict_c(Level<float> F, Level<float> C, Coefs<float> K) {
-  pdl_enter();
+__device__ __forceinline__ void residual_restrict_c_body(int bx, Level<float> F, Level<float> C, Coefs<float> K) {
   constexpr int TX = DIM == 3 ? 8 : 16;
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = (bx * blockDim.x + threadIdx.x) >> 5;
   const int tiles_x = (F.nx + TX - 1) / TX;
   const int tiles_y = F.ny >> 1;
   const int tiles_z = DIM == 3 ? (F.nz >> 1) : 1;
@@ -261,6 +266,12 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict_c(Level<float> F, 
   C.mu[q] = C.mu0[q] = w * v[4];
   C.p[q] = C.p0[q] = w * v[5];
   C.phib[q] = w * v[6];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_residual_restrict_c(Level<float> F, Level<float> C, Coefs<float> K) {
+  pdl_enter();
+  residual_restrict_c_body<DIM>(blockIdx.x, F, C, K);
 }
 
 }  // namespace chhs_dev

@@ -313,9 +313,8 @@ __device__ __forceinline__ void restrict_coef_at(const Level<U>& F, const Level<
 // A level's coefficients, and the restriction of phi^m and phi* to the next
 // level (has_next), in one pass.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_coef_restrict(Level<T> L, Coefs<T> K, Level<T> Cn, int has_next) {
-  pdl_enter();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void coef_restrict_body(int bx, Level<T> L, Coefs<T> K, Level<T> Cn, int has_next) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= L.ncell) return;
   int i, j, k;
   cell_ijk(c, L.nx, L.ny, i, j, k);
@@ -323,6 +322,12 @@ __global__ void __launch_bounds__(kBlock) k_coef_restrict(Level<T> L, Coefs<T> K
   auto pm = [&](int e) { return L.phim[e]; };
   coef_at<T, DIM>(L, K, c, i, j, k, ps, pm(c));
   if (has_next && !(i & 1) && !(j & 1) && (DIM == 2 || !(k & 1))) restrict_coef_at<T, T, DIM>(L, Cn, i, j, k, pm, ps);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_coef_restrict(Level<T> L, Coefs<T> K, Level<T> Cn, int has_next) {
+  pdl_enter();
+  coef_restrict_body<T, DIM>(blockIdx.x, L, K, Cn, has_next);
 }
 
 // ---------------------------------------------------------------- smoother
@@ -577,14 +582,19 @@ __global__ void __launch_bounds__(96) k_smooth_split(Level<double> L, Coefs<doub
 // f_c += N_c(R u) on every cell (used when there is no pre-smoothing sweep to
 // carry it).
 template <typename T, int DIM, bool CORR>
-__global__ void __launch_bounds__(kBlock) k_coarse_rhs(Level<T> C, Coefs<T> K) {
-  pdl_enter();
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void coarse_rhs_body(int bx, Level<T> C, Coefs<T> K) {
+  int q = bx * blockDim.x + threadIdx.x;
   if (q >= C.ncell) return;
   int i, j, k;
   cell_ijk(q, C.nx, C.ny, i, j, k);
   T f1, f2, f3;
   cell_rhs<T, DIM, CORR>(C, K, q, i, j, k, true, f1, f2, f3);
+}
+
+template <typename T, int DIM, bool CORR>
+__global__ void __launch_bounds__(kBlock) k_coarse_rhs(Level<T> C, Coefs<T> K) {
+  pdl_enter();
+  coarse_rhs_body<T, DIM, CORR>(blockIdx.x, C, K);
 }
 
 // ---------------------------------------------------------------- transfers
@@ -747,9 +757,8 @@ __global__ void __launch_bounds__(96) k_residual_restrict_split(Level<double> F,
 
 // u += P(u_c - u_c^0), P piecewise constant.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
-  pdl_enter();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void prolong_body(int bx, Level<T> F, Level<T> C) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= F.ncell) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
@@ -757,6 +766,12 @@ __global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
   F.phi[c] += C.phi[q] - C.phi0[q];
   F.mu[c] += C.mu[q] - C.mu0[q];
   F.p[c] += C.p[q] - C.p0[q];
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_prolong(Level<T> F, Level<T> C) {
+  pdl_enter();
+  prolong_body<T, DIM>(blockIdx.x, F, C);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -926,10 +941,9 @@ __global__ void __launch_bounds__(kBlock) k_norm(Level<T> L, Coefs<T> K, double*
 // The single-precision finest level of a step: phi^m and phi* rounded, its
 // coefficients, and the restriction to the next single-precision level.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_coef_restrict_f32(Level<double> F, Level<float> G, Coefs<float> K,
+__device__ __forceinline__ void coef_restrict_f32_body(int bx, Level<double> F, Level<float> G, Coefs<float> K,
                                                               Level<float> Gn, int has_next) {
-  pdl_enter();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= F.ncell) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
@@ -940,6 +954,13 @@ __global__ void __launch_bounds__(kBlock) k_coef_restrict_f32(Level<double> F, L
   coef_at<float, DIM>(G, K, c, i, j, k, ps, pm(c));
   if (has_next && !(i & 1) && !(j & 1) && (DIM == 2 || !(k & 1)))
     restrict_coef_at<float, double, DIM>(F, Gn, i, j, k, pm, ps);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_coef_restrict_f32(Level<double> F, Level<float> G, Coefs<float> K,
+                                                              Level<float> Gn, int has_next) {
+  pdl_enter();
+  coef_restrict_f32_body<DIM>(blockIdx.x, F, G, K, Gn, has_next);
 }
 
 // Double to single precision with integer instructions, truncating toward
@@ -963,15 +984,14 @@ __device__ __forceinline__ float f64_to_f32_rz(double x) {
 // right-hand side of the next inner solve: f32 = r cut to single precision,
 // e = 0, phi_b = phi cut to single precision.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<double> K, Level<float> G,
+__device__ __forceinline__ void norm_mixed_body(int bx, int nbx, Level<double> L, Coefs<double> K, Level<float> G,
                                                        double* partials, DevState* st,
                                                        cudaGraphConditionalHandle cond, int mode, int use_cond) {
-  pdl_enter();
   __shared__ bool last;
   double acc[2] = {0.0, 0.0};
   double mx = 0.0;
-  const int stride = gridDim.x * blockDim.x;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += stride) {
+  const int stride = nbx * blockDim.x;
+  for (int c = bx * blockDim.x + threadIdx.x; c < L.ncell; c += stride) {
     int i, j, k;
     cell_ijk(c, L.nx, L.ny, i, j, k);
     double n1, n2, n3;
@@ -994,26 +1014,38 @@ __global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<do
   block_sum<2>(acc);
   mx = block_max(mx);
   if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x] = acc[0];
-    partials[3 * blockIdx.x + 1] = acc[1];
-    partials[3 * blockIdx.x + 2] = mx;
+    partials[3 * bx] = acc[0];
+    partials[3 * bx + 1] = acc[1];
+    partials[3 * bx + 2] = mx;
     __threadfence();
-    last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    last = atomicAdd(&st->ticket, 1u) == nbx - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  norm_finish(partials, gridDim.x, L.ncell, st, cond, mode, use_cond);
+  norm_finish(partials, nbx, L.ncell, st, cond, mode, use_cond);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<double> K, Level<float> G,
+                                                       double* partials, DevState* st,
+                                                       cudaGraphConditionalHandle cond, int mode, int use_cond) {
+  pdl_enter();
+  norm_mixed_body<DIM>(blockIdx.x, gridDim.x, L, K, G, partials, st, cond, mode, use_cond);
 }
 
 // u <- u + e in double precision.
-static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L, Level<float> G) {
-  pdl_enter();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+static __device__ __forceinline__ void mixed_update_body(int bx, Level<double> L, Level<float> G) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= L.ncell) return;
   L.phi[c] += (double)G.phi[c];
   L.mu[c] += (double)G.mu[c];
   L.p[c] += (double)G.p[c];
+}
+
+static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L, Level<float> G) {
+  pdl_enter();
+  mixed_update_body(blockIdx.x, L, G);
 }
 
 // ---------------------------------------------------------------- step frame
@@ -1025,12 +1057,11 @@ static __global__ void __launch_bounds__(kBlock) k_mixed_update(Level<double> L,
 // Fused: the finest level's coefficients (phi* of the neighbours formed on
 // the fly) and the restriction of phi^m, phi* to the next level (has_next).
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_setup_coef(Level<double> L, const double* phimm1, double eps2,
+__device__ __forceinline__ void setup_coef_body(int bx, Level<double> L, const double* phimm1, double eps2,
                                                        const DevState* st, Coefs<double> K, Level<double> Cn,
                                                        int has_next) {
-  pdl_enter();
   if (st->failed) return;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= L.ncell) return;
   int i, j, k;
   cell_ijk(c, L.nx, L.ny, i, j, k);
@@ -1058,11 +1089,18 @@ __global__ void __launch_bounds__(kBlock) k_setup_coef(Level<double> L, const do
     restrict_coef_at<double, double, DIM>(L, Cn, i, j, k, pmf, psf);
 }
 
-// Accept the step: phi^{m-1} <- phi^m, phi^m <- phi^{m+1}, p <- p - mean(p).
-static __global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, double* phimm1, DevState* st) {
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_setup_coef(Level<double> L, const double* phimm1, double eps2,
+                                                       const DevState* st, Coefs<double> K, Level<double> Cn,
+                                                       int has_next) {
   pdl_enter();
+  setup_coef_body<DIM>(blockIdx.x, L, phimm1, eps2, st, K, Cn, has_next);
+}
+
+// Accept the step: phi^{m-1} <- phi^m, phi^m <- phi^{m+1}, p <- p - mean(p).
+static __device__ __forceinline__ void advance_body(int bx, Level<double> L, double* phimm1, DevState* st) {
   if (st->failed) return;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = bx * blockDim.x + threadIdx.x;
   if (c == 0) {
     st->steps_done += 1;
     st->vtotal += st->vcycles;
@@ -1071,6 +1109,11 @@ static __global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, doub
   phimm1[c] = L.phim[c];
   L.phim[c] = L.phi[c];
   L.p[c] -= st->pmean;
+}
+
+static __global__ void __launch_bounds__(kBlock) k_advance(Level<double> L, double* phimm1, DevState* st) {
+  pdl_enter();
+  advance_body(blockIdx.x, L, phimm1, st);
 }
 
 // ---------------------------------------------------------------- coarse tail
@@ -1364,8 +1407,7 @@ __device__ __forceinline__ Level<T> tail_level(const Tail<T>& tl, int l, unsigne
 }
 
 template <typename T, int DIM, bool CORR>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(Tail<T> tl, Coefs<T> K) {
-  pdl_enter();
+__device__ __forceinline__ void tail_body(const Tail<T>& tl, const Coefs<T>& K) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
   const int n = tl.n;
   // Copy in: per cell, every field is loaded before any is stored, so a
@@ -1427,6 +1469,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(Tail<T> tl, Coefs<T> K
   copy(G.phi, S.phi, G.ncell);
   copy(G.mu, S.mu, G.ncell);
   copy(G.p, S.p, G.ncell);
+}
+
+template <typename T, int DIM, bool CORR>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const __grid_constant__ Tail<T> tl, Coefs<T> K) {
+  pdl_enter();
+  tail_body<T, DIM, CORR>(tl, K);
 }
 
 // ---------------------------------------------------------------- diagnostics

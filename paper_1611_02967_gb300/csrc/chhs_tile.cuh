@@ -127,14 +127,13 @@ __device__ __forceinline__ void tile_N(const TileView<T, CORR>& V, int s, int SW
 }
 
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
+__device__ __forceinline__ void tile_body(int bx, int by, Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
                                                       int halo, int rhs, int prolong, int restrict_out,
                                                       TileOut<T> out) {
   // The tiles serve the correction-form (single-precision) levels only: the
   // plain form's right-hand side f_mu carries the shift of cubic_P, which
   // tile_N does not.
   static_assert(CORR, "k_tile runs the correction form only");
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char tile_smem[];
   const int SW = kTileW + 2 * halo, SH = kTileH + 2 * halo, SN = SW * SH;
   TileView<T, CORR> V;
@@ -145,7 +144,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
     V.phib = CORR ? base + 8 * SN : nullptr;
   }
   const int nx = L.nx, ny = L.ny;
-  const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;  // tile origin (global)
+  const int tx0 = bx * kTileW, ty0 = by * kTileH;  // tile origin (global)
   const int gx0 = tx0 - halo, gy0 = ty0 - halo;                      // shared-memory origin (global)
 
   // load the tile and its halo (cells outside the domain are never read);
@@ -306,6 +305,14 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, 
       }
     }
   }
+}
+
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
+                                                      int halo, int rhs, int prolong, int restrict_out,
+                                                      TileOut<T> out) {
+  pdl_enter();
+  tile_body<T, CORR>(blockIdx.x, blockIdx.y, L, Cl, K, npass, halo, rhs, prolong, restrict_out, out);
 }
 
 }  // namespace chhs_dev

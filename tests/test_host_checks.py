@@ -119,6 +119,8 @@ HANDLE_CALLS = {
     "chhs_server_result": (None, 0, None, None, None, None, None),
     "chhs_server_release": (None, 0),
     "chhs_server_stats": (None, None, None, None, None),
+    "chhs_batch_step": (None, 1, None, None, None),
+    "chhs_batch_launch_counts": (None, None, None),
 }
 
 
@@ -135,7 +137,8 @@ def test_every_handle_entry_point_is_covered():
     # a new entry point taking a handle gets a NULL case above
     handle_free = {"chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_create_ext",
                    "chhs_energy_noalloc", "chhs_server_create", "chhs_num_levels", "chhs_destroy",
-                   "chhs_last_error", "chhs_server_destroy"}
+                   "chhs_last_error", "chhs_server_destroy", "chhs_batch_workspace_bytes", "chhs_batch_create",
+                   "chhs_batch_size", "chhs_batch_run", "chhs_batch_last_error", "chhs_batch_destroy"}
     assert set(chhs.EXPORTS) - handle_free == set(HANDLE_CALLS)
 
 
@@ -222,3 +225,35 @@ def test_binding_buffer_checks():
     with pytest.raises(ValueError):
         chhs._buf(torch.zeros(24, dtype=torch.float64)[::2], 12)  # strided view
     assert chhs._buf(None, 12) == (None, 0, None)
+
+
+def _descs(specs):
+    arr = (chhs.chhs_run_desc * len(specs))()
+    for q, (dim, n, h, eps, gamma, dt) in enumerate(specs):
+        arr[q] = chhs.chhs_run_desc(dim, (ctypes.c_int * 3)(*n), h, eps, gamma, dt)
+    return arr
+
+
+def test_batch_arguments_checked_before_any_cuda_call(L):
+    good = (2, (64, 64, 1), 0.025, 0.05, 1.0, 0.005)
+    mixed = chhs.default_opts(precision=1)
+    one = _descs([good])
+    assert L.chhs_batch_workspace_bytes(1, one, ctypes.byref(mixed)) > 0
+    assert L.chhs_batch_workspace_bytes(1, one, None) > 0  # NULL opts: the mixed-precision defaults
+    # no runs, runs of two dimensions, a bad run, the double-precision form
+    assert L.chhs_batch_workspace_bytes(0, one, None) == 0
+    assert L.chhs_batch_workspace_bytes(2, _descs([good, (3, (16, 16, 16), 0.1, 0.05, 1.0, 0.005)]), None) == 0
+    assert L.chhs_batch_workspace_bytes(2, _descs([good, (2, (64, 64, 1), -0.1, 0.05, 1.0, 0.005)]), None) == 0
+    assert L.chhs_batch_workspace_bytes(1, one, ctypes.byref(chhs.default_opts(precision=0))) == 0
+    out = ctypes.c_void_p(1234)
+    assert L.chhs_batch_create(0, one, None, None, ctypes.byref(out)) == INVALID and not out.value
+    assert L.chhs_batch_create(1, one, None, None, None) == INVALID
+    # the batch's hierarchies are the runs' own, summed
+    two = _descs([good, (2, (128, 32, 1), 0.025, 0.05, 1.0, 0.005)])
+    w1 = L.chhs_workspace_bytes(2, (ctypes.c_int * 3)(64, 64, 1), ctypes.byref(mixed))
+    w2 = L.chhs_workspace_bytes(2, (ctypes.c_int * 3)(128, 32, 1), ctypes.byref(mixed))
+    assert L.chhs_batch_workspace_bytes(2, two, None) >= w1 + w2
+    # NULL batch
+    assert L.chhs_batch_step(None, 1, None, None, None) == INVALID
+    assert L.chhs_batch_size(None) == 0 and L.chhs_batch_run(None, 0) is None
+    L.chhs_batch_destroy(None)
