@@ -65,6 +65,9 @@ typedef struct {
                           interfaces): at eps/h = 0.4, gamma = 4 on 64^3 it left a pointwise
                           error in phi of 1.2e-9; the default guard brings that to 4.9e-10 and
                           adds no V-cycles on the 512^2 and 128^3 workloads. */
+    int coarsest_f64;  /* mixed form: 1 solves the coarsest grid of every single-precision V-cycle
+                          in double precision, 0 (default) in single precision; the double form
+                          always solves it in double.  Not 0 or 1: CHHS_ERR_INVALID_ARG. */
 } chhs_opts;
 
 /* Fill *opts with the defaults above.  Returns CHHS_ERR_INVALID_ARG on NULL. */

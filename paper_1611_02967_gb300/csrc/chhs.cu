@@ -124,7 +124,8 @@ Layout make_layout(int dim, const int n[3], int coarsest, int precision) {
 // pressure problem is singular and the face count 0 has no inverse).
 bool valid_opts(const chhs_opts& o) {
   return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.max_v >= 1 && o.coarsest >= 2 &&
-         o.tol > 0 && (o.precision == 0 || o.precision == 1) && o.max_factor >= 0;
+         o.tol > 0 && (o.precision == 0 || o.precision == 1) && o.max_factor >= 0 &&
+         (o.coarsest_f64 == 0 || o.coarsest_f64 == 1);
 }
 
 bool valid_problem(int dim, const int n[3], double h, double eps, double gamma, double dt) {
@@ -452,7 +453,7 @@ struct Enqueue {
   static size_t tail_bytes(const Tail<T>& tail) {
     int nc[kTailMaxLevels];
     for (int l = 0; l < tail.n; ++l) nc[l] = tail.lev[l].ncell;
-    return tail_smem_bytes<T, DIM, CORR>(nc, tail.n);
+    return tail_smem_bytes<T, DIM, CORR>(nc, tail.n, tail.coarsest_f64);
   }
 
   // Opt the tail kernel in to the shared memory its levels need.
@@ -756,6 +757,7 @@ void fill_tail(Tail<T>& tail, const std::vector<Level<T>>& lev, int start, const
   tail.nu1 = o.nu1;
   tail.nu2 = o.nu2;
   tail.top_rhs = start > 0 ? 1 : 0;
+  tail.coarsest_f64 = (sizeof(T) == 4 && o.coarsest_f64) ? 1 : 0;
 }
 
 // The first level of the one-block tail: the coarsest, and every level above
@@ -880,6 +882,7 @@ chhs_status chhs_default_opts(chhs_opts* o) {
   o->tol = 1e-10;
   o->precision = 0;
   o->max_factor = 50.0;
+  o->coarsest_f64 = 0;
   return CHHS_OK;
 }
 

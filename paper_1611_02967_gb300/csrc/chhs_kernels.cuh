@@ -1129,6 +1129,7 @@ struct Tail {
   int n;        // levels in the tail; the last one is the coarsest
   int nu1, nu2;
   int top_rhs;  // complete the FAS right-hand side of the tail's top level first
+  int coarsest_f64;  // single-precision correction form: solve the coarsest grid in double precision
 };
 
 // Groups of three warps in the tail block for the split update (warp 15 idles).
@@ -1377,9 +1378,11 @@ __host__ __device__ constexpr int tail_fields() { return 22 + (DIM == 3 ? 2 : 0)
 __host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
 
 template <typename T, int DIM, bool CORR>
-__host__ __device__ inline size_t tail_smem_bytes(const int* ncell, int n) {
+__host__ __device__ inline size_t tail_smem_bytes(const int* ncell, int n, int coarsest_f64 = 0) {
   size_t b = 0;
   for (int l = 0; l < n; ++l) b += tail_fields<DIM, CORR>() * tail_align(sizeof(T) * ncell[l]);
+  // the double-precision copy of the coarsest grid (coarsest_solve_f64)
+  if (coarsest_f64 && n > 0) b += tail_fields<DIM, CORR>() * tail_align(sizeof(double) * ncell[n - 1]);
   return b;
 }
 
@@ -1404,6 +1407,46 @@ __device__ __forceinline__ Level<T> tail_level(const Tail<T>& tl, int l, unsigne
   if (CORR) L.phib = carve();
   L.phis = nullptr;
   return L;
+}
+
+// The coarsest solve of a single-precision correction-form V-cycle carried
+// out in double precision: the coarsest grid's fields are widened into a
+// double-precision copy (its per-step coefficients, computed in single
+// precision, are widened exactly), the sweeps and the stopping test of
+// coarsest_solve run on the copy, and the correction is rounded back.
+template <int DIM>
+__device__ __forceinline__ void coarsest_solve_f64(const Level<float>& S, const Coefs<float>& K,
+                                                   unsigned char* smem) {
+  Level<double> D;
+  D.nx = S.nx; D.ny = S.ny; D.nz = S.nz; D.ncell = S.ncell;
+  D.rnx = S.rnx; D.rny = S.rny; D.rhw = S.rhw;
+  D.ih2 = S.ih2; D.h2 = S.h2; D.sih2 = S.sih2; D.e34ih2 = S.e34ih2;
+  const size_t st = tail_align(sizeof(double) * S.ncell);
+  int q = 0;
+  auto carve = [&]() { return reinterpret_cast<double*>(smem + (q++) * st); };
+  const float* src[22] = {S.phi, S.mu, S.p, S.fphi, S.fmu, S.fp, S.phim, S.phib, S.ax, S.ay, S.Mx, S.My,
+                          S.sM, S.sa, S.cAe, S.cC, S.cGn, S.cHn, S.cQ, S.cH, S.az, S.Mz};
+  D.phi = carve(); D.mu = carve(); D.p = carve(); D.fphi = carve(); D.fmu = carve(); D.fp = carve();
+  D.phim = carve(); D.phib = carve(); D.ax = carve(); D.ay = carve(); D.Mx = carve(); D.My = carve();
+  D.sM = carve(); D.sa = carve(); D.cAe = carve(); D.cC = carve(); D.cGn = carve(); D.cHn = carve();
+  D.cQ = carve(); D.cH = carve();
+  D.az = DIM == 3 ? carve() : nullptr;
+  D.Mz = DIM == 3 ? carve() : nullptr;
+  D.phis = D.phi0 = D.mu0 = D.p0 = nullptr;
+  double* dst[22] = {D.phi, D.mu, D.p, D.fphi, D.fmu, D.fp, D.phim, D.phib, D.ax, D.ay, D.Mx, D.My,
+                     D.sM, D.sa, D.cAe, D.cC, D.cGn, D.cHn, D.cQ, D.cH, D.az, D.Mz};
+  const int nf = DIM == 3 ? 22 : 20;
+  for (int f = 0; f < nf; ++f)
+    for (int c = threadIdx.x; c < S.ncell; c += blockDim.x) dst[f][c] = (double)src[f][c];
+  __syncthreads();
+  const Coefs<double> KD{(double)K.s, (double)K.gamma, (double)K.e34};
+  coarsest_solve<double, DIM, true>(D, KD);
+  for (int c = threadIdx.x; c < S.ncell; c += blockDim.x) {
+    S.phi[c] = (float)D.phi[c];
+    S.mu[c] = (float)D.mu[c];
+    S.p[c] = (float)D.p[c];
+  }
+  __syncthreads();
 }
 
 template <typename T, int DIM, bool CORR>
@@ -1455,7 +1498,17 @@ __device__ __forceinline__ void tail_body(const Tail<T>& tl, const Coefs<T>& K) 
   {
     const Level<T> Lc = tail_level<T, DIM, CORR>(tl, n - 1, tail_smem);
     if (n > 1 || tl.top_rhs) tail_rhs<T, DIM, CORR>(Lc, K);
-    coarsest_solve<T, DIM, CORR>(Lc, K);
+    if constexpr (sizeof(T) == 4 && CORR) {
+      if (tl.coarsest_f64) {
+        size_t off = 0;
+        for (int q = 0; q < n; ++q) off += tail_fields<DIM, CORR>() * tail_align(sizeof(T) * tl.lev[q].ncell);
+        coarsest_solve_f64<DIM>(Lc, K, tail_smem + off);
+      } else {
+        coarsest_solve<T, DIM, CORR>(Lc, K);
+      }
+    } else {
+      coarsest_solve<T, DIM, CORR>(Lc, K);
+    }
   }
   for (int l = n - 2; l >= 0; --l) {
     const Level<T> L = tail_level<T, DIM, CORR>(tl, l, tail_smem);
