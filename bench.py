@@ -50,8 +50,29 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # reciprocal (8), dmu (2), dp (2), the three updates (3) = 44 (phi^m / 4 is a
 # stored per-step constant).
 SMOOTH_FLOPS = {2: 8 * 4 - 4 + 44, 3: 8 * 6 - 4 + 44}
+# The byte model of one smoothing pass per cell (both colours, in order): read
+# phi, mu, p, phi^m, phi*, f_mu and write phi, mu, p, nine values; per colour
+# launch half of it per cell of the level.  In double precision 72 B per cell
+# updated; in the single-precision correction form the pass reads the
+# correction (3), the right-hand sides (3), phi^m, phi* and phi_b and writes
+# the correction, twelve 4-byte values: 24 B per cell of the level per colour
+# launch.
+SMOOTH_BYTES_F64 = 72.0
+SMOOTH_BYTES_F32_PER_CELL_PER_COLOUR = 24.0
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of this GPU pool written
+    beside the repository, else the recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (copy bandwidth of this pool's GB300s)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
 KERNEL_SRC = os.path.join(ROOT, "paper_1611_02967_gb300", "csrc", "chhs_kernels.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_smooth_spinodal512.txt")
+KERNEL_SRC_3D = os.path.join(ROOT, "paper_1611_02967_gb300", "csrc", "chhs_corr3.cuh")
+TRAFFIC_FILE_3D = os.path.join(ROOT, "profiles", "k_smooth_c_bubbles128.txt")
 
 
 def parse_args(argv=None):
@@ -124,17 +145,25 @@ def kernel_hash():
     return hashlib.sha256(src[:cut if cut > 0 else len(src)]).hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per k_smooth launch from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+def file_hash(path):
+    """Hash of a kernel source file (a recorded traffic figure holds while it matches)."""
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(path=None, src=None):
+    """DRAM bytes per launch of the profiled kernel from a committed ncu
+    summary (default: the double-precision smoother's), if it was taken on
+    the current kernel source; else None."""
+    path = path or TRAFFIC_FILE
     try:
         vals = {}
-        with open(TRAFFIC_FILE) as f:
+        with open(path) as f:
             for line in f:
                 if "=" in line and not line.startswith("#"):
                     k, v = line.split("=", 1)
                     vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_sha256_16") != kernel_hash():
+        if vals.get("kernel_source_sha256_16") != (kernel_hash() if src is None else file_hash(src)):
             return None
         return float(vals["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -196,6 +225,23 @@ class ClockSampler:
         reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_info():
+    """(model name, online cores) of the host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count()
 
 
 def oracle_rate(w, max_seconds=15.0, max_steps=40, skip_first=True):
@@ -262,7 +308,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(config(1), l2="not applicable (host CPU)"),
             "vcycles_per_step": sum(vs) / len(vs),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_info()[0], "nproc": cpu_info()[1]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -376,13 +423,38 @@ def served_leg(capacity_cell_steps_per_s, seed=5, nruns=60):
             "vcycles_per_step": float(sum(r["vcycles"] for r in res) / steps.sum()), "sample": SERVED_DESC}
 
 
+def e2e_steps(run, state, steps, ncell):
+    """K steps through the public API with the state in pinned host memory:
+    each step copies (phi^m, phi^{m-1}, mu, p) in, solves, and copies them
+    out.  Returns (seconds, bytes in per step, bytes out per step)."""
+    import torch
+
+    from paper_1611_02967_gb300 import chhs
+    host = [torch.empty(s_.shape, dtype=torch.float64, pin_memory=True).numpy() for s_ in state]
+    for h_, s_ in zip(host, state):
+        h_[...] = s_
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run.set_state(*host)
+        run.step(1)
+        chhs.lib().chhs_get_state(run.handle, *[chhs._buf(h_, ncell, True)[0] for h_ in host], 0)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, 4 * 8 * ncell, 4 * 8 * ncell
+
+
 def bubbles_leg(stream, flush, steps=10, warmup=3):
-    """The 128^3 bubble workload (3D, eps 0.04, gamma 2, dt 0.005): both forms,
-    device-timed like the main line, from the same state after warm-up."""
+    """The 128^3 bubble workload (3D, eps 0.04, gamma 2, dt 0.005), the
+    largest single-run configuration: both forms device-timed like the main
+    line from the same state after warm-up, each with its end-to-end rate
+    through the public API (host state copied in and out every step), and the
+    HBM roofline of the mixed form's dominant memory-bound kernel, the
+    finest-level single-precision colour pass."""
     from paper_1611_02967_gb300 import chhs, inputs
     w = inputs.workload("bubbles128")
+    ncell = 128 ** 3
     out = {"workload": "3D bubbles 128^3 on (0,6.4)^3, eps 0.04, gamma 2, dt 0.005, 8 tanh bubbles (seed 3)",
-           "steps": steps}
+           "steps": steps, "l2": "inputs larger than L2 (the 128^3 hierarchy is ~400 MB), and flushed between steps"}
     state = None
     for prec, key in ((0, "f64"), (1, "mixed")):
         run = chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream,
@@ -393,37 +465,88 @@ def bubbles_leg(stream, flush, steps=10, warmup=3):
             state = run.get_state()
         run.set_state(*state)
         tune = run.autotune(2)
+        run.set_state(*state)
         ms, v, r = time_steps(run, steps, stream, flush)
-        out[key] = {"value": 128 ** 3 * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-                    "vcycles_per_step": v / steps, "final_resid": r, "tuning": tune}
+        secs, bi, bo = e2e_steps(run, state, steps, ncell)
+        out[key] = {"value": ncell * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                    "vcycles_per_step": v / steps, "final_resid": r, "tuning": tune,
+                    "e2e": {"value": ncell * steps / secs, "unit": UNIT, "h2d_bytes_per_step": bi,
+                            "d2h_bytes_per_step": bo}}
+        if prec == 1:
+            run.set_state(*state)
+            run.step(1)
+            t = run.profile_smooth32(100) / 1e3
+            alg = SMOOTH_BYTES_F32_PER_CELL_PER_COLOUR * ncell
+            gbs, src = hbm_peak()
+            out[key]["roofline"] = {
+                "bound": "hbm", "kernel": "k_smooth_c<3> on the 128^3 level (single-precision colour pass, "
+                                          "coefficients recomputed from phi*)",
+                "achieved": alg / t / 1e9, "peak": gbs, "unit": "GB/s", "frac": alg / t / 1e9 / gbs,
+                "peak_source": src, "traffic": measured_traffic(TRAFFIC_FILE_3D, KERNEL_SRC_3D),
+                "algorithmic_bytes_per_launch": alg, "avg_launch_us": 1e6 * t,
+                "duration_source": "100 launches back to back between CUDA events (chhs_profile_smooth32)",
+                "note": "24 B per cell per colour launch: the twelve 4-byte values of a sweep (read correction, "
+                        "right-hand sides, phi^m, phi*, phi_b; write the correction) split over its two launches"}
         run.close()
     return out
 
 
-def batched_leg(seed=4, nruns=256, steps=100):
-    """The batched workload in full: 256 runs of sizes drawn from
-    {64..1024}^2, eps U(0.02,0.08), gamma U(0.5,4), h 0.025, dt 0.005, 100
-    steps each, mixed precision, all submitted at once to the request loop
-    (32 runs on the device at a time); aggregate cell-steps/s."""
+def batched_runs(seed=4, nruns=256):
+    """The batched workload's runs: sizes drawn from {64..1024}^2, eps
+    U(0.02,0.08), gamma U(0.5,4), h 0.025, dt 0.005, seeded spinodal data."""
     import numpy as np
 
-    from paper_1611_02967_gb300 import chhs, inputs
+    from paper_1611_02967_gb300 import inputs
     u = inputs.uniform01(seed, nruns * 3, stream=13).reshape(nruns, 3)
     sizes = np.array([64, 128, 256, 512, 1024])[np.minimum((u[:, 0] * 5).astype(int), 4)]
+    runs = [((int(n), int(n)), 0.025, 0.02 + 0.06 * u[k, 1], 0.5 + 3.5 * u[k, 2], 0.005) for k, n in enumerate(sizes)]
     phis = [inputs.spinodal((int(n), int(n)), seed * 1000 + k, mean=0.0) for k, n in enumerate(sizes)]
-    with chhs.Server(pool_bytes=16 << 30, max_active=32, steps_per_slice=5) as sv:
-        ids = [sv.submit((int(n), int(n)), 0.025, 0.02 + 0.06 * u[k, 1], 0.5 + 3.5 * u[k, 2], 0.005, steps,
-                         phis[k], precision=1) for k, n in enumerate(sizes)]
-        for rid in ids:
-            sv.wait(rid, 600.0)
-        res = [sv.result(rid, with_phi=False) for rid in ids]
-    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    return runs, phis, sizes
+
+
+def batched_leg(seed=4, nruns=256, steps=100, request_loop=True):
+    """The batched workload in full (256 runs, 100 steps each, mixed
+    precision) through chhs_batch: one graph of batched launches, one per
+    kernel and multigrid level over all runs, timed with CUDA events on the
+    batch's stream (creation and initial data untimed).  For comparison the
+    same runs also go through the request loop (32 runs on per-run streams)."""
+    import numpy as np
+    import torch
+
+    from paper_1611_02967_gb300 import chhs
+    runs, phis, sizes = batched_runs(seed, nruns)
     work = float((sizes.astype(float) ** 2).sum() * steps)
-    return {"value": work / span, "unit": UNIT, "runs": nruns, "steps_each": steps, "seconds": span,
-            "all_converged": all(r["status"] == 0 for r in res),
-            "sample": "%d runs (sizes drawn from {64..1024}^2, seed 4), %d steps each, all submitted at "
-                      "t = 0 to the request loop (32 slots, mixed precision)%s" % (
-                          nruns, steps, "; the full batched configuration" if (nruns, steps) == (256, 100) else "")}
+    stream = torch.cuda.Stream()
+    with chhs.Batch(runs, stream=stream.cuda_stream) as b:
+        for k in range(nruns):
+            b.runs[k].set_phi(phis[k])
+        per_v, per_step = b.launch_counts()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, v, r = b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+    out = {"value": work / secs, "unit": UNIT, "runs": nruns, "steps_each": steps, "seconds": secs,
+           "all_converged": all(x == 0 for x in st), "vcycles_per_step": float(np.mean(v)) / steps,
+           "launches_per_vcycle": per_v, "launches_per_step_frame": per_step,
+           "sample": "%d runs (sizes drawn from {64..1024}^2, seed 4), %d steps each, one chhs_batch (mixed "
+                     "precision)%s" % (nruns, steps, "; the full batched configuration" if (nruns, steps) == (256, 100)
+                                       else "")}
+    if request_loop:
+        with chhs.Server(pool_bytes=16 << 30, max_active=32, steps_per_slice=5) as sv:
+            ids = [sv.submit(sh, h, eps, gamma, dt, steps, phis[k], precision=1)
+                   for k, (sh, h, eps, gamma, dt) in enumerate(runs)]
+            for rid in ids:
+                sv.wait(rid, 600.0)
+            res = [sv.result(rid, with_phi=False) for rid in ids]
+        span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+        out["request_loop"] = {"value": work / span, "unit": UNIT, "seconds": span,
+                               "all_converged": all(x["status"] == 0 for x in res),
+                               "sample": "the same runs submitted at t = 0 to the request loop (32 slots, per-run "
+                                         "streams and graphs), wall clock from first submit to last result"}
+    return out
 
 
 def run_ours(args):
@@ -495,10 +618,19 @@ def run_ours(args):
     avg_s = run.profile_smooth(200) / 1e3
     achieved = flops_per_launch / avg_s / 1e12
     traffic = measured_traffic()
+    fp64_peak = max(chhs.probe_fp64() for _ in range(3))
+    cells_per_launch = sm_units / sm_launch
+    hbm_bytes = SMOOTH_BYTES_F64 * cells_per_launch
+    hbm_gbs, hbm_src = hbm_peak()
     roofline = {"bound": "alu", "kernel": "k_smooth<double,2,false> on the 512x512 level (FP64 red-black cell update)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal FP64 152 SMs x 2.07 GHz x 4 flop/clk (recipe's unit counts)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "peak_source": "measured: chhs_probe_fp64 (FP64 FMA chains on every SM, best of 3) in this run",
+                "peak_nominal": FP64_PEAK_TFLOPS, "frac_of_nominal": achieved / FP64_PEAK_TFLOPS,
+                "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / avg_s / 1e9,
+                        "peak_gbs": hbm_gbs, "peak_source": hbm_src, "frac": hbm_bytes / avg_s / 1e9 / hbm_gbs,
+                        "note": "72 B per cell updated (read phi, mu, p, phi^m, phi*, f_mu; write phi, mu, p), "
+                                "the hot-path table's byte model; this kernel is bound by the FP64 pipe"},
                 "traffic": traffic, "flop_per_launch": flops_per_launch,
                 "avg_launch_us": 1e6 * avg_s, "avg_launch_us_eager": 1e3 * sm_ms / sm_launch,
                 "duration_source": "200 finest-level passes back to back between CUDA events (chhs_profile_smooth)",
@@ -543,9 +675,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, nsteps, secs = oracle_rate(w)
+        model, ncores = cpu_info()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "time steps 2..%d of the same 512x512 workload (%.1f s), single-threaded" % (
-                   nsteps + 1, secs)}
+                   nsteps + 1, secs), "cpu_model": model, "nproc": ncores}
     run.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

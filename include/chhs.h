@@ -175,20 +175,44 @@ chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_o
  * has no counterpart in the paper. */
 chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass);
 
+/* The single-precision finest-level smoothing launch of a mixed-precision
+ * handle, alone: in 2D one pre-smoothing tile launch (nu1 sweeps fused with
+ * the residual and its restriction), in 3D one colour pass of the
+ * correction-form smoother; npasses launches back to back (after one
+ * untimed launch) between two CUDA events on the handle's stream, and
+ * *ms_per_launch = their average duration.  The run's state is unchanged
+ * (the launches' own outputs are scratch that every V-cycle rewrites; the
+ * finest correction is put back); nothing is allocated.  Blocks until done.
+ * Errors: CHHS_ERR_INVALID_ARG (null pointer, npasses < 1, steps pending, a
+ * double-precision handle, or a grid whose finest level is in the one-block
+ * tail), CHHS_ERR_CUDA.  For profiling; it has no counterpart in the paper. */
+chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launch);
+
+/* Measured double-precision throughput of the current device: a kernel of
+ * independent fused multiply-add chains on every SM, timed with CUDA events;
+ * *tflops_out in TFLOP/s (2 flops per FMA).  The roofline denominator of the
+ * double-precision smoother.  Errors: CHHS_ERR_INVALID_ARG (NULL),
+ * CHHS_ERR_CUDA.  No counterpart in the paper. */
+chhs_status chhs_probe_fp64(double* tflops_out);
+
 /* Launch shapes of one handle (see chhs_autotune). */
 typedef struct {
   int tail_cells;     /* levels with at most this many cells run in the one-block tail */
   int split_threads;  /* double-precision levels with at most this many cells per colour
                          use the three-warp split update (0: never) */
   int tile_threads;   /* threads per tile in the 2D mixed form */
+  int coarse_nu1;     /* pre- and post-smoothing sweeps on the levels below the finest (the finest */
+  int coarse_nu2;     /* keeps opts->nu1, nu2) */
   double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
                          the setting in force was timed (every candidate failed, or the fastest
                          could not be rebuilt and the original setting was kept) */
 } chhs_tuning;
 
-/* Autotuner of the handle's launch shapes: tries candidate settings (where
- * the one-block tail starts; in double precision, up to which level size the
- * split update is used; in the 2D mixed form, the tile block size), times
+/* Autotuner of the handle's launch shapes and coarse sweep counts: tries
+ * candidate settings (where the one-block tail starts; in double precision,
+ * up to which level size the split update is used; in the 2D mixed form, the
+ * tile block size; the sweeps on the levels below the finest: the options'
+ * nu1, nu2 or, when both exceed 1, one each), times
  * trial_steps steps of the handle's own problem from its current state with
  * each, keeps the fastest and rebuilds the step graph with it.  The state is
  * restored after every trial and at the end, so the run continues exactly
@@ -200,6 +224,14 @@ typedef struct {
  * CHHS_ERR_CUDA.  The paper has no counterpart (launch shapes are a property
  * of this implementation). */
 chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out);
+
+/* Apply a tuning (for instance one chhs_autotune chose for another run of
+ * the same shape) and rebuild the step graph; ms_per_step is ignored.  The
+ * state is kept.  Errors: CHHS_ERR_INVALID_ARG (NULL, steps pending, a run
+ * of a batch, tail_cells < 1, split_threads < 0, tile_threads not a multiple
+ * of 32 in 32..1024, coarse sweep counts < 0 or both 0, or a setting the
+ * grid cannot take -- the previous tuning is then kept), CHHS_ERR_CUDA. */
+chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* tuning);
 
 /* Discrete mass (phi^m, 1) = h^d sum phi^m (Section 4, mass conservation). */
 chhs_status chhs_mass(chhs_t* run, double* mass_out);
@@ -387,6 +419,14 @@ chhs_status chhs_batch_step(chhs_batch_t* batch, int nsteps, int* status_out, in
 /* Launches of the batch's step graph: per V-cycle and per step outside the
  * V-cycle loop, whatever the number of runs. */
 chhs_status chhs_batch_launch_counts(const chhs_batch_t* batch, int* per_vcycle, int* per_step);
+
+/* One time step of every run launched kernel by kernel (no graph) with a
+ * CUDA event pair around each batched launch; adds into the caller's arrays
+ * of CHHS_K_COUNT entries the device milliseconds and launches per kernel
+ * kind (as chhs_profile_step).  For profiling: the host reads the "any run
+ * iterating" flag after every V-cycle.  Errors: CHHS_ERR_INVALID_ARG (NULL
+ * argument), CHHS_ERR_CUDA. */
+chhs_status chhs_batch_profile_step(chhs_batch_t* batch, double* ms_out, long long* launches_out);
 
 /* Text of the batch's last error ("" if none). */
 const char* chhs_batch_last_error(const chhs_batch_t* batch);

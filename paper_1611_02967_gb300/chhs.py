@@ -29,7 +29,8 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_server_create", "chhs_server_submit", "chhs_server_wait", "chhs_server_result",
            "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity",
            "chhs_autotune", "chhs_batch_workspace_bytes", "chhs_batch_create", "chhs_batch_size", "chhs_batch_run",
-           "chhs_batch_step", "chhs_batch_launch_counts", "chhs_batch_last_error", "chhs_batch_destroy"]
+           "chhs_batch_step", "chhs_batch_launch_counts", "chhs_batch_last_error", "chhs_batch_destroy",
+           "chhs_profile_smooth32", "chhs_probe_fp64", "chhs_batch_profile_step", "chhs_set_tuning"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
@@ -55,7 +56,7 @@ class chhs_run_desc(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """chhs_tuning (include/chhs.h)."""
     _fields_ = [("tail_cells", ctypes.c_int), ("split_threads", ctypes.c_int), ("tile_threads", ctypes.c_int),
-                ("ms_per_step", ctypes.c_double)]
+                ("coarse_nu1", ctypes.c_int), ("coarse_nu2", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
 
 
 class ChhsError(RuntimeError):
@@ -116,6 +117,10 @@ def lib():
             "chhs_batch_launch_counts": (i, [_vp, _ip, _ip]),
             "chhs_batch_last_error": (ctypes.c_char_p, [_vp]),
             "chhs_batch_destroy": (None, [_vp]),
+            "chhs_profile_smooth32": (i, [_vp, i, _dp]),
+            "chhs_probe_fp64": (i, [_dp]),
+            "chhs_batch_profile_step": (i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+            "chhs_set_tuning": (i, [_vp, ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -295,6 +300,14 @@ class Run:
         self._check(lib().chhs_profile_smooth(self.handle, int(npasses), ctypes.byref(ms)))
         return ms.value
 
+    def profile_smooth32(self, npasses=100):
+        """Average ms of the mixed form's single-precision finest-level
+        smoothing launch (2D: the pre-smoothing tile launch; 3D: one colour
+        pass), timed back to back."""
+        ms = ctypes.c_double(0.0)
+        self._check(lib().chhs_profile_smooth32(self.handle, int(npasses), ctypes.byref(ms)))
+        return ms.value
+
     def velocity(self):
         """Face velocities of the last accepted step (Eq. 2.3): array (dim,) +
         shape, [a][c] on the face between cell c and its +a neighbour."""
@@ -310,7 +323,12 @@ class Run:
         t = Tuning()
         self._check(lib().chhs_autotune(self.handle, int(trial_steps), ctypes.byref(t)))
         return dict(tail_cells=t.tail_cells, split_threads=t.split_threads, tile_threads=t.tile_threads,
-                    ms_per_step=t.ms_per_step)
+                    coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2, ms_per_step=t.ms_per_step)
+
+    def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2):
+        """chhs_set_tuning: apply launch shapes and coarse sweep counts."""
+        t = Tuning(int(tail_cells), int(split_threads), int(tile_threads), int(coarse_nu1), int(coarse_nu2), 0.0)
+        self._check(lib().chhs_set_tuning(self.handle, ctypes.byref(t)))
 
     def mass(self):
         m = ctypes.c_double(0.0)
@@ -460,6 +478,21 @@ class Batch:
             raise ChhsError(st, lib().chhs_batch_last_error(self.handle).decode())
         return list(s_), list(v_), list(r_)
 
+    def profile_step(self, acc=None):
+        """One step of every run launched kernel by kernel with events;
+        accumulates {kind: [ms, launches]}."""
+        n = len(K_NAMES)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_longlong * n)()
+        st = lib().chhs_batch_profile_step(self.handle, ms, la)
+        if st != CHHS_OK:
+            raise ChhsError(st, lib().chhs_batch_last_error(self.handle).decode())
+        acc = acc if acc is not None else {k: [0.0, 0] for k in K_NAMES}
+        for q, k in enumerate(K_NAMES):
+            acc[k][0] += ms[q]
+            acc[k][1] += la[q]
+        return acc
+
     def launch_counts(self):
         a, b = ctypes.c_int(0), ctypes.c_int(0)
         lib().chhs_batch_launch_counts(self.handle, ctypes.byref(a), ctypes.byref(b))
@@ -483,3 +516,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def probe_fp64():
+    """Measured FP64 FMA throughput of the current device in TFLOP/s."""
+    t = ctypes.c_double(0.0)
+    st = lib().chhs_probe_fp64(ctypes.byref(t))
+    if st != CHHS_OK:
+        raise ChhsError(st, "chhs_probe_fp64 failed")
+    return t.value

@@ -181,6 +181,7 @@ struct chhs {
   // tile_threads threads
   int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kTileThreads;
   int norm_blocks = 1;              // grid of the stopping-norm kernels (whole blocks per SM)
+  int nu1c = 2, nu2c = 2;           // sweeps on the levels below the finest (chhs_autotune; opts by default)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
@@ -285,6 +286,11 @@ struct Enqueue {
     return Coefs<T>{T(run->dt), T(run->gamma), T(0.75 * run->eps * run->eps)};
   }
 
+  // Sweeps before and after the coarse-grid correction on level l: the
+  // options' counts on the finest level, the handle's coarse counts below.
+  static int nu_pre(const chhs_t* run, int l) { return l == 0 ? run->opts.nu1 : run->nu1c; }
+  static int nu_post(const chhs_t* run, int l) { return l == 0 ? run->opts.nu2 : run->nu2c; }
+
   // sweeps red-black sweeps; with rhs the first one also completes the FAS
   // right-hand side of this (coarse) level.
   template <typename T, bool CORR>
@@ -331,7 +337,7 @@ struct Enqueue {
       // restriction in one tiled launch, prolongation + post-smoothing in another
       const dim3 grid((L.nx + kTileW - 1) / kTileW, (L.ny + kTileH - 1) / kTileH);
       const int nf = tile_nfields<CORR>();
-      const int np1 = 2 * run->opts.nu1, np2 = 2 * run->opts.nu2;
+      const int np1 = 2 * nu_pre(run, l), np2 = 2 * nu_post(run, l);
       // the pre-smoothing launch writes the second copy of the state (and the
       // completed right-hand side), the post-smoothing launch reads them and
       // writes the state back: no launch writes what its own tiles read
@@ -351,18 +357,18 @@ struct Enqueue {
         to_state.mu64 = run->lev[0].mu;
         to_state.p64 = run->lev[0].p;
       }
-      launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu1, [&] {
+      launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_pre(run, l), [&] {
         pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
                  np1 + 1, rhs ? 1 : 0, 0, 1, to_copy);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
-      launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * run->opts.nu2, [&] {
+      launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_post(run, l), [&] {
         pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T)), s, Lb, C, K, np2, np2,
                  0, 1, 0, to_state);
       });
       return;
     }
-    if (rhs && run->opts.nu1 == 0)
+    if (rhs && nu_pre(run, l) == 0)
       launch(run, s, CHHS_K_COARSE_RHS, L.ncell, [&] {
         pdl(k_coarse_rhs<T, DIM, CORR>, nblocks(L.ncell), kBlock, s, L, K);
       });
@@ -370,7 +376,7 @@ struct Enqueue {
       corr_vcycle_level(run, s, lev, tail, l);
       return;
     }
-    smooth<T, CORR>(run, s, L, run->opts.nu1, rhs && run->opts.nu1 > 0);
+    smooth<T, CORR>(run, s, L, nu_pre(run, l), rhs && nu_pre(run, l) > 0);
     constexpr int TX = DIM == 3 ? 8 : 16;
     const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
     const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
@@ -387,7 +393,7 @@ struct Enqueue {
     launch(run, s, CHHS_K_PROLONG, L.ncell, [&] {
       pdl(k_prolong<T, DIM>, nblocks(L.ncell), kBlock, s, L, C);
     });
-    smooth<T, CORR>(run, s, L, run->opts.nu2, false);
+    smooth<T, CORR>(run, s, L, nu_post(run, l), false);
   }
 
   // 3D single-precision (correction-form) levels above the tail: colour
@@ -407,7 +413,7 @@ struct Enqueue {
     const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
     const int kind = l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH;
     const Level<double> none{};
-    const int nu1 = run->opts.nu1, nu2 = run->opts.nu2;
+    const int nu1 = nu_pre(run, l), nu2 = nu_post(run, l);
     for (int it = 0; it < nu1; ++it)
       for (int colour = 0; colour < 2; ++colour)
         launch(run, s, kind, colour_cells(L, colour), [&] {
@@ -484,7 +490,7 @@ struct Enqueue {
                   "the grid does not coarsen to a coarsest level small enough for the one-block solve");
     CU(raise_to(ktail, smem));
     if constexpr (use_tiles<T>()) {
-      const int halo = 2 * std::max(run->opts.nu1, run->opts.nu2) + 1;
+      const int halo = 2 * std::max(std::max(run->opts.nu1, run->opts.nu2), std::max(run->nu1c, run->nu2c)) + 1;
       const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T));
       const void* ktile = reinterpret_cast<const void*>(k_tile<T, CORR>);
       if (!fits(ktile, tb))
@@ -751,11 +757,11 @@ Level<T> make_level(const chhs_t* run, const Shape& sh, int l, char* base, bool 
 }
 
 template <typename T>
-void fill_tail(Tail<T>& tail, const std::vector<Level<T>>& lev, int start, const chhs_opts& o) {
+void fill_tail(Tail<T>& tail, const std::vector<Level<T>>& lev, int start, const chhs_opts& o, int nu1c, int nu2c) {
   tail.n = 0;
   for (int l = start; l < (int)lev.size(); ++l) tail.lev[tail.n++] = lev[l];
-  tail.nu1 = o.nu1;
-  tail.nu2 = o.nu2;
+  tail.nu1 = start > 0 ? nu1c : o.nu1;
+  tail.nu2 = start > 0 ? nu2c : o.nu2;
   tail.top_rhs = start > 0 ? 1 : 0;
   tail.coarsest_f64 = (sizeof(T) == 4 && o.coarsest_f64) ? 1 : 0;
 }
@@ -770,8 +776,8 @@ void place_tail(chhs_t* run) {
   while (run->tail_start > 0 && cells(run->tail_start - 1) <= run->tail_cells &&
          nl - (run->tail_start - 1) <= kTailMaxLevels)
     --run->tail_start;
-  fill_tail(run->tail, run->lev, run->tail_start, run->opts);
-  fill_tail(run->tail32, run->lev32, run->tail_start, run->opts);
+  fill_tail(run->tail, run->lev, run->tail_start, run->opts, run->nu1c, run->nu2c);
+  fill_tail(run->tail32, run->lev32, run->tail_start, run->opts, run->nu1c, run->nu2c);
 }
 
 chhs_status setup_handle(chhs_t* run) {
@@ -784,6 +790,8 @@ chhs_status setup_handle(chhs_t* run) {
   for (size_t l = 0; l < Lo.level32_off.size(); ++l)
     run->lev32.push_back(make_level<float>(run, Lo.shapes[l], (int)l, run->arena + Lo.level32_off[l], true));
   run->tail_cells = run->opts.precision == 1 ? kTailCellsF32 : kTailCellsF64;
+  run->nu1c = run->opts.nu1;
+  run->nu2c = run->opts.nu2;
   place_tail(run);
   // The norm kernels loop over cells with the grid's stride: kNormBlocksPerSM
   // blocks on every SM (all resident at once), so no SM holds a block more
@@ -1050,25 +1058,157 @@ chhs_status chhs_profile_smooth(chhs_t* run, int npasses, double* ms_per_pass) {
   return CHHS_OK;
 }
 
+chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launch) {
+  if (!run || npasses < 1 || !ms_per_launch) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
+  if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
+  if (run->opts.precision != 1 || run->tail_start == 0)
+    return fail(run, CHHS_ERR_INVALID_ARG, "needs a mixed-precision handle whose finest level is not in the tail");
+  run->err.clear();
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CU(cudaEventCreate(&ev.a));
+  CU(cudaEventCreate(&ev.b));
+  const Level<float>& L = run->lev32[0];
+  const Level<float>& C = run->lev32[1];
+  const Coefs<float> K{(float)run->dt, (float)run->gamma, (float)(0.75 * run->eps * run->eps)};
+  // the finest single-precision level's correction is scratch between steps
+  // (the stopping norm rewrites it), but it is kept and put back all the same
+  // (in its R u arrays, which only the coarser levels use); the launches also
+  // write the next level and the tiles' second copy, which every V-cycle
+  // rewrites before reading
+  const size_t bytes = sizeof(float) * (size_t)L.ncell;
+  CU(cudaMemcpyAsync(L.phi0, L.phi, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.mu0, L.mu, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.p0, L.p, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
+  const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
+  const int np1 = 2 * run->opts.nu1;
+  const TileOut<float> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3, nullptr, nullptr, nullptr};
+  const dim3 grid((L.nx + kTileW - 1) / kTileW, (L.ny + kTileH - 1) / kTileH);
+  for (int k = 0; k <= npasses; ++k) {
+    if (k == 1) CU(cudaEventRecord(ev.a, run->stream));
+    if (run->dim == 3)
+      pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
+    else
+      pdl_grid(k_tile<float, true>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4),
+               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy);
+  }
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(ev.b, run->stream));
+  CU(cudaMemcpyAsync(L.phi, L.phi0, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.mu, L.mu0, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaMemcpyAsync(L.p, L.p0, bytes, cudaMemcpyDeviceToDevice, run->stream));
+  CU(cudaStreamSynchronize(run->stream));
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
+  *ms_per_launch = ms / npasses;
+  return CHHS_OK;
+}
+
+// Throughput of the FP64 pipe: every thread runs 8 independent chains of
+// fused multiply-adds (x <- x a + b) in double precision.
+__global__ void k_fp64_probe(double a, double b, int iters, double* sink) {
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = threadIdx.x * 1e-3 + q;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  if (s == 12345.678) sink[0] = s;  // keeps the chains live; never true for these inputs
+}
+
+chhs_status chhs_probe_fp64(double* tflops_out) {
+  chhs_t* run = nullptr;
+  if (!tflops_out) return CHHS_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  const int blocks = nsm * 8, threads = 256, iters = 4096;
+  k_fp64_probe<<<blocks, threads>>>(0.999999, 1e-7, 64, nullptr);  // warm-up
+  cudaEventRecord(e0);
+  k_fp64_probe<<<blocks, threads>>>(0.999999, 1e-7, iters, nullptr);
+  cudaEventRecord(e1);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return CHHS_ERR_CUDA;
+  *tflops_out = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+  return CHHS_OK;
+}
+
+chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
+  if (!run || !t) return fail(run, CHHS_ERR_INVALID_ARG, "NULL argument");
+  if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
+  if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
+  if (t->tail_cells < 1 || t->split_threads < 0 || t->tile_threads < 32 || t->tile_threads > 1024 ||
+      t->tile_threads % 32 != 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 || t->coarse_nu1 + t->coarse_nu2 < 1)
+    return fail(run, CHHS_ERR_INVALID_ARG, "invalid tuning");
+  run->err.clear();
+  CU(cudaStreamSynchronize(run->stream));
+  const int keep[5] = {run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c};
+  auto rebuild = [&](int tc, int sp, int tt, int n1, int n2) -> chhs_status {
+    if (run->exec) cudaGraphExecDestroy(run->exec);
+    if (run->graph) cudaGraphDestroy(run->graph);
+    run->exec = nullptr;
+    run->graph = nullptr;
+    run->tail_cells = tc;
+    run->split_threads = sp;
+    run->tile_threads = tt;
+    run->nu1c = n1;
+    run->nu2c = n2;
+    place_tail(run);
+    return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
+  };
+  chhs_status s = rebuild(t->tail_cells, t->split_threads, t->tile_threads, t->coarse_nu1, t->coarse_nu2);
+  if (s != CHHS_OK) {
+    const std::string why = run->err;
+    if (rebuild(keep[0], keep[1], keep[2], keep[3], keep[4]) != CHHS_OK)
+      return fail(run, CHHS_ERR_CUDA, "could not rebuild the step graph");
+    return fail(run, s, why.empty() ? "tuning refused" : why);
+  }
+  return CHHS_OK;
+}
+
 chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   if (!run || trial_steps < 1) return fail(run, CHHS_ERR_INVALID_ARG, "bad argument");
   if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   run->err.clear();
   struct Cand {
-    int tail_cells, split_threads, tile_threads;
+    int tail_cells, split_threads, tile_threads, nu1c, nu2c;
   };
   std::vector<Cand> cands;
   const bool mixed = run->opts.precision == 1;
-  if (!mixed) {
-    const int tails[2] = {64, run->dim == 2 ? 256 : 512};
-    for (int tc : tails)
-      for (int sp : {0, 8192, 32768}) cands.push_back({tc, sp, run->tile_threads});
-  } else if (run->dim == 2) {
-    for (int tc : {256, 1024, 2048})
-      for (int tt : {256, 512}) cands.push_back({tc, run->split_threads, tt});
-  } else {
-    for (int tc : {64, 512}) cands.push_back({tc, run->split_threads, run->tile_threads});
+  // sweep counts below the finest level: the options' own, and one sweep
+  // each way when the options ask for more (fewer passes on the small,
+  // latency-bound levels; the V-cycle counts the trials measure decide)
+  std::vector<std::pair<int, int>> coarse = {{run->opts.nu1, run->opts.nu2}};
+  if (run->opts.nu1 > 1 && run->opts.nu2 > 1) coarse.push_back({1, 1});
+  for (const auto& cn : coarse) {
+    if (!mixed) {
+      const int tails[2] = {64, run->dim == 2 ? 256 : 512};
+      for (int tc : tails)
+        for (int sp : {0, 8192, 32768}) cands.push_back({tc, sp, run->tile_threads, cn.first, cn.second});
+    } else if (run->dim == 2) {
+      for (int tc : {256, 1024, 2048})
+        for (int tt : {256, 512}) cands.push_back({tc, run->split_threads, tt, cn.first, cn.second});
+    } else {
+      for (int tc : {64, 512}) cands.push_back({tc, run->split_threads, run->tile_threads, cn.first, cn.second});
+    }
   }
   // the run's state (phi^m, phi^{m-1}, mu, p), restored before every trial and at the end
   const size_t nc = (size_t)run->ncell(), bytes = sizeof(double) * nc;
@@ -1108,10 +1248,12 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     run->tail_cells = c.tail_cells;
     run->split_threads = c.split_threads;
     run->tile_threads = c.tile_threads;
+    run->nu1c = c.nu1c;
+    run->nu2c = c.nu2c;
     place_tail(run);
     return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
   };
-  const Cand orig{run->tail_cells, run->split_threads, run->tile_threads};
+  const Cand orig{run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c};
   Cand best = orig;
   float best_ms = -1.f;
   chhs_status s;
@@ -1144,6 +1286,8 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     out->tail_cells = run->tail_cells;
     out->split_threads = run->split_threads;
     out->tile_threads = run->tile_threads;
+    out->coarse_nu1 = run->nu1c;
+    out->coarse_nu2 = run->nu2c;
     out->ms_per_step = best_ms < 0.f ? -1.0 : (double)best_ms / trial_steps;
   }
   return CHHS_OK;
@@ -1332,7 +1476,8 @@ struct BatchStep {
 
   // Launch one batched kernel (or, when planning, lay out its tables).
   template <class J, typename... KArgs, typename... Args>
-  void go(const JobList<J>& jl, void (*kernel)(KArgs...), int block, size_t smem, cudaStream_t s, Args... extra) {
+  void go(int kind, const JobList<J>& jl, void (*kernel)(KArgs...), int block, size_t smem, cudaStream_t s,
+          Args... extra) {
     if (jl.jobs.empty()) return;
     if (!capture) {
       offs.push_back(put(jl.jobs.data(), sizeof(J) * jl.jobs.size()));
@@ -1342,7 +1487,23 @@ struct BatchStep {
     const J* dj = reinterpret_cast<const J*>(b->tables + offs[cur++]);
     const int* ds = reinterpret_cast<const int*>(b->tables + offs[cur++]);
     if (counter) ++*counter;
-    pdl_smem(kernel, jl.blocks(), block, smem, s, dj, ds, jl.njobs(), extra...);
+    timed(kind, [&] { pdl_smem(kernel, jl.blocks(), block, smem, s, dj, ds, jl.njobs(), extra...); }, s);
+  }
+
+  // Event pairs around the launches while profiling (chhs_batch_profile_step).
+  Prof* prof = nullptr;
+  template <class F>
+  void timed(int kind, F&& f, cudaStream_t s) {
+    if (!prof) {
+      f();
+      return;
+    }
+    cudaEvent_t a = prof->next(), e = prof->next();
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(e, s);
+    prof->kind.push_back(kind);
+    prof->units.push_back(1.0);
   }
 
   // The tail launch: one block per job, no prefix sum.
@@ -1354,7 +1515,8 @@ struct BatchStep {
     }
     const TailJob<float>* dj = reinterpret_cast<const TailJob<float>*>(b->tables + offs[cur++]);
     if (counter) ++*counter;
-    pdl_smem(kb_tail<float, DIM, true>, (int)jobs.size(), kTailThreads, tail_smem, s, dj);
+    timed(CHHS_K_COARSEST, [&] { pdl_smem(kb_tail<float, DIM, true>, (int)jobs.size(), kTailThreads, tail_smem, s, dj); },
+          s);
   }
 
   static Coefs<float> k32(const chhs_t* r) { return Enqueue<DIM>::template coefs<float>(r); }
@@ -1372,7 +1534,7 @@ struct BatchStep {
       const Level<double>& F = r->lev[0];
       jl.add(SetupJob{F, F, r->phimm1, r->eps * r->eps, r->st, k64(r), 0}, nblocks(F.ncell));
     }
-    go(jl, kb_setup_coef<DIM>, kBlock, 0, s);
+    go(CHHS_K_FRAME, jl, kb_setup_coef<DIM>, kBlock, 0, s);
   }
 
   void coefs(cudaStream_t s) {
@@ -1384,7 +1546,7 @@ struct BatchStep {
       jf.add(CoefF32Job{r->lev[0], r->lev32[0], ng > 1 ? r->lev32[1] : r->lev32[0], k32(r), ng > 1 ? 1 : 0},
              nblocks(r->lev[0].ncell));
     }
-    go(jf, kb_coef_restrict_f32<DIM>, kBlock, 0, s);
+    go(CHHS_K_FRAME, jf, kb_coef_restrict_f32<DIM>, kBlock, 0, s);
     for (int l = 1; l < maxng; ++l) {
       JobList<CoefJob> jl;
       for (chhs_t* r : b->runs) {
@@ -1393,7 +1555,7 @@ struct BatchStep {
         const Level<float>& G = r->lev32[l];
         jl.add(CoefJob{G, l + 1 < ng ? r->lev32[l + 1] : G, k32(r), l + 1 < ng ? 1 : 0}, nblocks(G.ncell));
       }
-      go(jl, kb_coef_restrict<DIM>, kBlock, 0, s);
+      go(CHHS_K_FRAME, jl, kb_coef_restrict<DIM>, kBlock, 0, s);
     }
   }
 
@@ -1401,7 +1563,7 @@ struct BatchStep {
     JobList<NormJob> jl;
     for (chhs_t* r : b->runs)
       jl.add(NormJob{r->lev[0], r->lev32[0], k64(r), r->partials, r->st}, r->norm_blocks);
-    go(jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cond, mode);
+    go(CHHS_K_NORM, jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cond, mode, b->d_ticket + 1);
   }
 
   void vcycle(cudaStream_t s) {
@@ -1416,7 +1578,7 @@ struct BatchStep {
     for (chhs_t* r : b->runs)
       if (!Enqueue<DIM>::fused_update(r))
         upd.add(PairJob{r->lev32[0], r->lev32[0], k32(r), r->lev[0], r->st}, nblocks(r->lev[0].ncell));
-    go(upd, kb_mixed_update, kBlock, 0, s);
+    go(CHHS_K_FRAME, upd, kb_mixed_update, kBlock, 0, s);
   }
 
   void pre(cudaStream_t s, int l, int nu1) {
@@ -1431,7 +1593,7 @@ struct BatchStep {
         jl.add(TileJob<float>{L, r->lev32[l + 1], k32(r), to_copy, r->st, np1, np1 + 1, l > 0 ? 1 : 0, 0, 1, gx},
                gx * gy);
       }
-      go(jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
+      go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
       return;
     }
     auto runs_at = [&](auto add) {
@@ -1443,7 +1605,7 @@ struct BatchStep {
       runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
         jl.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, nblocks(L.ncell));
       });
-      go(jl, kb_coarse_rhs<DIM>, kBlock, 0, s);
+      go(CHHS_K_COARSE_RHS, jl, kb_coarse_rhs<DIM>, kBlock, 0, s);
     }
     for (int it = 0; it < nu1; ++it)
       for (int colour = 0; colour < 2; ++colour) {
@@ -1453,7 +1615,7 @@ struct BatchStep {
           jl.add(SmoothCJob{L, C, Level<double>{}, k32(r), r->st, colour, (l > 0 && it == 0) ? 1 : 0, 0},
                  (threads + kSmoothBlock - 1) / kSmoothBlock);
         });
-        go(jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
+        go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
       }
     JobList<PairJob> jr;
     runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
@@ -1461,7 +1623,7 @@ struct BatchStep {
       const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
       jr.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, (int)((tiles * 32 + kBlock - 1) / kBlock));
     });
-    go(jr, kb_residual_restrict_c<DIM>, kBlock, 0, s);
+    go(CHHS_K_RESTRICT, jr, kb_residual_restrict_c<DIM>, kBlock, 0, s);
   }
 
   void post(cudaStream_t s, int l, int nu2) {
@@ -1489,7 +1651,7 @@ struct BatchStep {
         const int gx = (L.nx + kTileW - 1) / kTileW, gy = (L.ny + kTileH - 1) / kTileH;
         jl.add(TileJob<float>{Lb, r->lev32[l + 1], k32(r), to_state, r->st, np2, np2, 0, 1, 0, gx}, gx * gy);
       }
-      go(jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
+      go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
       return;
     }
     auto runs_at = [&](auto add) {
@@ -1501,7 +1663,7 @@ struct BatchStep {
       runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
         jl.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, nblocks(L.ncell));
       });
-      go(jl, kb_prolong<DIM>, kBlock, 0, s);
+      go(CHHS_K_PROLONG, jl, kb_prolong<DIM>, kBlock, 0, s);
       return;
     }
     for (int it = 0; it < nu2; ++it)
@@ -1514,14 +1676,14 @@ struct BatchStep {
           jl.add(SmoothCJob{L, C, upd ? r->lev[0] : Level<double>{}, k32(r), r->st, colour, 0, pro},
                  (threads + kSmoothBlock - 1) / kSmoothBlock);
         });
-        go(jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
+        go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
       }
   }
 
   void advance(cudaStream_t s) {
     JobList<AdvanceJob> jl;
     for (chhs_t* r : b->runs) jl.add(AdvanceJob{r->lev[0], r->phimm1, r->st}, nblocks(r->lev[0].ncell));
-    go(jl, kb_advance, kBlock, 0, s);
+    go(CHHS_K_FRAME, jl, kb_advance, kBlock, 0, s);
   }
 
   // Plan: lay out every table in emission order (no CUDA calls).
@@ -1635,6 +1797,35 @@ struct BatchStep {
     b->launches_per_step = n_frame;
     return CHHS_OK;
   }
+
+  // One step launched kernel by kernel with events (the loop decided on the
+  // host from the "any run iterating" flag of the batched norm).
+  chhs_status profile(Prof* p) {
+    plan();  // the same emission order as the captured graph
+    capture = true;
+    cur = 0;
+    prof = p;
+    cudaStream_t s = b->stream;
+    setup(s);
+    coefs(s);
+    norm(s, 0, 0);
+    const size_t vcycle_cur = cur;
+    for (int v = 0;; ++v) {
+      unsigned int go_host = 0;
+      BCU(cudaMemcpyAsync(&go_host, b->d_ticket + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+      BCU(cudaStreamSynchronize(s));
+      if (!go_host) break;
+      cur = vcycle_cur;
+      vcycle(s);
+      norm(s, 0, 1);
+    }
+    cur = offs.size() - 2;  // the advance's jobs and prefix sum come last
+    advance(s);
+    prof = nullptr;
+    BCU(cudaGetLastError());
+    BCU(cudaStreamSynchronize(s));
+    return CHHS_OK;
+  }
 };
 
 void batch_free(chhs_batch_t* b) {
@@ -1742,7 +1933,7 @@ chhs_status chhs_batch_create(int nruns, const chhs_run_desc* runs, const chhs_o
   chhs_status s = CHHS_OK;
   const size_t out_bytes = (2 * sizeof(int) + sizeof(double)) * nruns;
   if (cudaMemcpy(b->d_sts, sts.data(), sizeof(DevState*) * nruns, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(b->d_ticket, 0, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(b->d_ticket, 0, 2 * sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&b->h_out, out_bytes) != cudaSuccess)
     s = CHHS_ERR_CUDA;
   if (s == CHHS_OK) {
@@ -1811,6 +2002,33 @@ chhs_status chhs_batch_launch_counts(const chhs_batch_t* b, int* per_vcycle, int
   if (!b || !per_vcycle || !per_step) return CHHS_ERR_INVALID_ARG;
   *per_vcycle = b->launches_per_v;
   *per_step = b->launches_per_step;
+  return CHHS_OK;
+}
+
+chhs_status chhs_batch_profile_step(chhs_batch_t* b, double* ms_out, long long* launches_out) {
+  if (!b || !ms_out || !launches_out) return bfail(b, CHHS_ERR_INVALID_ARG, "NULL argument");
+  b->err.clear();
+  const int n = b->nruns;
+  kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max_of(b->opts), b->opts.max_v);
+  BCU(cudaGetLastError());
+  Prof prof;
+  chhs_status s;
+  if (b->dim == 2) {
+    BatchStep<2> bs{b};
+    bs.prepare();
+    s = bs.profile(&prof);
+  } else {
+    BatchStep<3> bs{b};
+    bs.prepare();
+    s = bs.profile(&prof);
+  }
+  if (s != CHHS_OK) return s;
+  for (size_t q = 0; q < prof.kind.size(); ++q) {
+    float ms = 0.f;
+    BCU(cudaEventElapsedTime(&ms, prof.ev[2 * q], prof.ev[2 * q + 1]));
+    ms_out[prof.kind[q]] += ms;
+    launches_out[prof.kind[q]] += 1;
+  }
   return CHHS_OK;
 }
 

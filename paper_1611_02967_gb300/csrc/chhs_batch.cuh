@@ -28,6 +28,20 @@ __device__ __forceinline__ int job_of(const int* start, int njobs, int b) {
   return lo;
 }
 
+// The block's job copied into shared memory by all its threads: the device
+// functions then read each field where they use it (a table in global
+// memory would have its fields held in registers across the whole kernel).
+template <class J>
+__device__ __forceinline__ const J& job_in_smem(const J* jobs, int j) {
+  __shared__ __align__(16) unsigned char buf[sizeof(J)];
+  static_assert(sizeof(J) % 4 == 0, "jobs are copied as 32-bit words");
+  const unsigned* src = reinterpret_cast<const unsigned*>(jobs + j);
+  unsigned* dst = reinterpret_cast<unsigned*>(buf);
+  for (int q = threadIdx.x; q < (int)(sizeof(J) / 4); q += blockDim.x) dst[q] = __ldg(src + q);
+  __syncthreads();
+  return *reinterpret_cast<const J*>(buf);
+}
+
 // A run still iterating in the V-cycle loop (its norm kernel set go).
 __device__ __forceinline__ bool gate_open(const DevState* gate) {
   return gate == nullptr || *(volatile const int*)&gate->go != 0;
@@ -95,12 +109,12 @@ struct NormJob {
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, const int* start, int njobs,
                                                         unsigned int* ticket, cudaGraphConditionalHandle cond,
-                                                        int mode) {
+                                                        int mode, unsigned int* any_out) {
   pdl_enter();
   __shared__ bool last_all;
   __shared__ int any_go;
   const int j = job_of(start, njobs, blockIdx.x);
-  const NormJob& J = jobs[j];
+  const NormJob& J = job_in_smem(jobs, j);
   if (mode == 0 || gate_open(J.st))
     norm_mixed_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode,
                          0);
@@ -119,7 +133,8 @@ __global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, con
   __syncthreads();
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    cudaGraphSetConditional(cond, any_go ? 1u : 0u);
+    *any_out = any_go ? 1u : 0u;
+    if (cond) cudaGraphSetConditional(cond, any_go ? 1u : 0u);
   }
 }
 
@@ -134,10 +149,10 @@ struct TileJob {
 };
 
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(kTileThreads, 2) kb_tile(const TileJob<T>* jobs, const int* start, int njobs) {
+__global__ void __launch_bounds__(kTileThreads, 3) kb_tile(const TileJob<T>* jobs, const int* start, int njobs) {
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
-  const TileJob<T>& J = jobs[j];
+  const TileJob<T>& J = job_in_smem(jobs, j);
   if (!gate_open(J.gate)) return;
   const int lb = blockIdx.x - start[j];
   const int by = lb / J.gx, bx = lb - by * J.gx;
@@ -169,10 +184,10 @@ struct SmoothCJob {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(kSmoothBlock, 6) kb_smooth_c(const SmoothCJob* jobs, const int* start, int njobs) {
+__global__ void __launch_bounds__(kSmoothBlock) kb_smooth_c(const SmoothCJob* jobs, const int* start, int njobs) {
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
-  const SmoothCJob& J = jobs[j];
+  const SmoothCJob& J = job_in_smem(jobs, j);
   if (!gate_open(J.gate)) return;
   smooth_c_body<DIM>(blockIdx.x - start[j], J.L, J.C, J.K, J.colour, J.rhs, J.pro, J.U);
 }
@@ -190,7 +205,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) kb_residual_restrict_c(const PairJob* jobs, const int* start, int njobs) {
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
-  const PairJob& J = jobs[j];
+  const PairJob& J = job_in_smem(jobs, j);
   if (!gate_open(J.gate)) return;
   residual_restrict_c_body<DIM>(blockIdx.x - start[j], J.F, J.C, J.K);
 }

@@ -126,8 +126,9 @@ __device__ __forceinline__ void n_corr(const Level<float>& L, const Coefs<float>
 //        form), u <- u + e in double precision for the pass's cell and for
 //        its x-neighbour of the other colour.
 template <int DIM>
-__device__ __forceinline__ void smooth_c_body(int bx, Level<float> L, Level<float> C, Coefs<float> K,
-                                                           int colour, int rhs, int pro, Level<double> U) {
+__device__ __forceinline__ void smooth_c_body(int bx, const Level<float>& L, const Level<float>& C,
+                                              const Coefs<float>& K, int colour, int rhs, int pro,
+                                              const Level<double>& U) {
   const int hw = (L.nx + 1) >> 1;
   const int t = bx * blockDim.x + threadIdx.x;
   int row, k;
@@ -201,8 +202,10 @@ __device__ __forceinline__ void smooth_c_body(int bx, Level<float> L, Level<floa
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kSmoothBlock) k_smooth_c(Level<float> L, Level<float> C, Coefs<float> K,
-                                                           int colour, int rhs, int pro, Level<double> U) {
+__global__ void __launch_bounds__(kSmoothBlock) k_smooth_c(const __grid_constant__ Level<float> L,
+                                                           const __grid_constant__ Level<float> C, Coefs<float> K,
+                                                           int colour, int rhs, int pro,
+                                                           const __grid_constant__ Level<double> U) {
   pdl_enter();
   smooth_c_body<DIM>(blockIdx.x, L, C, K, colour, rhs, pro, U);
 }
@@ -212,7 +215,8 @@ __global__ void __launch_bounds__(kSmoothBlock) k_smooth_c(Level<float> L, Level
 // with recomputed coefficients.  Writes u_c = u_c^0 = R e, f_c = R r and
 // phi_b,c = R phi_b.
 template <int DIM>
-__device__ __forceinline__ void residual_restrict_c_body(int bx, Level<float> F, Level<float> C, Coefs<float> K) {
+__device__ __forceinline__ void residual_restrict_c_body(int bx, const Level<float>& F, const Level<float>& C,
+                                                         const Coefs<float>& K) {
   constexpr int TX = DIM == 3 ? 8 : 16;
   const int lane = threadIdx.x & 31;
   const int warp = (bx * blockDim.x + threadIdx.x) >> 5;
@@ -269,7 +273,9 @@ __device__ __forceinline__ void residual_restrict_c_body(int bx, Level<float> F,
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_residual_restrict_c(Level<float> F, Level<float> C, Coefs<float> K) {
+__global__ void __launch_bounds__(kBlock) k_residual_restrict_c(const __grid_constant__ Level<float> F,
+                                                                const __grid_constant__ Level<float> C,
+                                                                Coefs<float> K) {
   pdl_enter();
   residual_restrict_c_body<DIM>(blockIdx.x, F, C, K);
 }

@@ -984,7 +984,8 @@ __device__ __forceinline__ float f64_to_f32_rz(double x) {
 // right-hand side of the next inner solve: f32 = r cut to single precision,
 // e = 0, phi_b = phi cut to single precision.
 template <int DIM>
-__device__ __forceinline__ void norm_mixed_body(int bx, int nbx, Level<double> L, Coefs<double> K, Level<float> G,
+__device__ __forceinline__ void norm_mixed_body(int bx, int nbx, const Level<double>& L, const Coefs<double>& K,
+                                                const Level<float>& G,
                                                        double* partials, DevState* st,
                                                        cudaGraphConditionalHandle cond, int mode, int use_cond) {
   __shared__ bool last;
@@ -1027,7 +1028,8 @@ __device__ __forceinline__ void norm_mixed_body(int bx, int nbx, Level<double> L
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_norm_mixed(Level<double> L, Coefs<double> K, Level<float> G,
+__global__ void __launch_bounds__(kBlock) k_norm_mixed(const __grid_constant__ Level<double> L, Coefs<double> K,
+                                                       const __grid_constant__ Level<float> G,
                                                        double* partials, DevState* st,
                                                        cudaGraphConditionalHandle cond, int mode, int use_cond) {
   pdl_enter();

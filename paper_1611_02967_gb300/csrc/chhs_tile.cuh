@@ -127,9 +127,9 @@ __device__ __forceinline__ void tile_N(const TileView<T, CORR>& V, int s, int SW
 }
 
 template <typename T, bool CORR>
-__device__ __forceinline__ void tile_body(int bx, int by, Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
-                                                      int halo, int rhs, int prolong, int restrict_out,
-                                                      TileOut<T> out) {
+__device__ __forceinline__ void tile_body(int bx, int by, const Level<T>& L, const Level<T>& Cl,
+                                          const Coefs<T>& K, int npass, int halo, int rhs, int prolong,
+                                          int restrict_out, const TileOut<T>& out) {
   // The tiles serve the correction-form (single-precision) levels only: the
   // plain form's right-hand side f_mu carries the shift of cubic_P, which
   // tile_N does not.
@@ -308,9 +308,10 @@ __device__ __forceinline__ void tile_body(int bx, int by, Level<T> L, Level<T> C
 }
 
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(kTileThreads) k_tile(Level<T> L, Level<T> Cl, Coefs<T> K, int npass,
+__global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Level<T> L,
+                                                      const __grid_constant__ Level<T> Cl, Coefs<T> K, int npass,
                                                       int halo, int rhs, int prolong, int restrict_out,
-                                                      TileOut<T> out) {
+                                                      const __grid_constant__ TileOut<T> out) {
   pdl_enter();
   tile_body<T, CORR>(blockIdx.x, blockIdx.y, L, Cl, K, npass, halo, rhs, prolong, restrict_out, out);
 }

@@ -4,7 +4,9 @@ s = 0.05 h, T = 0.8, tol 1e-10), fine grids 32, 64, 128 and 256.
 
 Calls only oracle/ (and the seedless Eq. 5.1 generator).  The Cauchy
 difference uses cell-centred bilinear interpolation with mirrored ghosts and
-the h_f-weighted l2 norm (the reading recorded in the design notes).
+the h_f-weighted l2 norm: Section 5.1 names bilinear interpolation and then
+matlab's "nearest", but nearest injection between cell-centred grids is first
+order and could not give the printed rates of 2, so bilinear is taken.
 Run: python tests/golden/make_e1_oracle.py  (a few minutes, single core).
 """
 import os

@@ -1,6 +1,6 @@
-"""chhs_autotune: the launch-shape autotuner leaves the run's state exactly as
-it was, picks one of its candidates, and the tuned handle's next step still
-matches the oracle within the form's tolerance."""
+"""chhs_autotune: the autotuner of launch shapes and coarse sweep counts leaves
+the run's state exactly as it was, picks one of its candidates, and the tuned
+handle's next steps still match the oracle within the form's tolerance."""
 import numpy as np
 import pytest
 
@@ -30,5 +30,30 @@ def test_autotune_keeps_state_and_steps_match_oracle(shape, precision):
             assert t["tail_cells"] in (256, 1024, 2048) and t["tile_threads"] in (256, 512)
         else:
             assert t["tail_cells"] in (64, 512)
+        assert (t["coarse_nu1"], t["coarse_nu2"]) in ((2, 2), (1, 1))
         for _ in range(2):
             _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape", [(256, 256), (32, 32, 32)])
+def test_one_coarse_sweep_reaches_the_same_answer(shape, precision):
+    """The coarse sweep counts the autotuner may choose change only the path
+    to the solution: with one sweep each way below the finest level
+    (chhs_set_tuning) the steps still equal the oracle's, and the state is
+    kept across the rebuild."""
+    h, eps, gamma, dt = (0.025, 0.05, 1.0, 0.005) if len(shape) == 2 else (0.05, 0.04, 2.0, 0.005)
+    phi0 = inputs.spinodal(shape, 43, mean=0.0, amplitude=0.05)
+    with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=precision)) as run:
+        run.set_phi(phi0)
+        run.step(2)
+        before = run.get_state()
+        t = run.autotune(2)
+        run.set_tuning(t["tail_cells"], t["split_threads"], t["tile_threads"], 1, 1)
+        for a, b in zip(before, run.get_state()):
+            assert np.array_equal(a, b)
+        for _ in range(2):
+            _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+        with pytest.raises(chhs.ChhsError):
+            run.set_tuning(t["tail_cells"], t["split_threads"], 100, 1, 1)  # not a multiple of 32
+        _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])

@@ -5,8 +5,11 @@ to 1e-10, fine grids 3.2/32 ... 3.2/512 (160 ... 2560 steps).  The GPU's
 Cauchy differences must equal the CPU oracle's (tests/golden/e1_oracle.txt,
 written by make_e1_oracle.py from oracle/ only) for the grids the oracle can
 afford, and the rates must be within 0.1 of the printed ones.  The printed
-error magnitudes themselves are not matched by either side (design notes,
-reading 12).
+error magnitudes themselves are not matched by either side: both give
+differences a steady factor of about 5 above the printed ones, and none of
+the readings tried on the oracle (norm normalisation, nearest or bilinear
+transfer, restriction-based comparison, start-up from a near-exact phi^1,
+other T, s or gamma) lands within two digits of them.
 """
 import os
 

@@ -121,6 +121,9 @@ HANDLE_CALLS = {
     "chhs_server_stats": (None, None, None, None, None),
     "chhs_batch_step": (None, 1, None, None, None),
     "chhs_batch_launch_counts": (None, None, None),
+    "chhs_profile_smooth32": (None, 1, None),
+    "chhs_batch_profile_step": (None, None, None),
+    "chhs_set_tuning": (None, None),
 }
 
 
@@ -138,7 +141,8 @@ def test_every_handle_entry_point_is_covered():
     handle_free = {"chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_create_ext",
                    "chhs_energy_noalloc", "chhs_server_create", "chhs_num_levels", "chhs_destroy",
                    "chhs_last_error", "chhs_server_destroy", "chhs_batch_workspace_bytes", "chhs_batch_create",
-                   "chhs_batch_size", "chhs_batch_run", "chhs_batch_last_error", "chhs_batch_destroy"}
+                   "chhs_batch_size", "chhs_batch_run", "chhs_batch_last_error", "chhs_batch_destroy",
+                   "chhs_probe_fp64"}
     assert set(chhs.EXPORTS) - handle_free == set(HANDLE_CALLS)
 
 
