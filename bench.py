@@ -238,6 +238,15 @@ def cpu_info():
                     break
     except OSError:
         pass
+    if model is None:  # Arm hosts list no model name in /proc/cpuinfo; lscpu does
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
     if model is None:
         import platform
         model = platform.processor() or platform.machine()

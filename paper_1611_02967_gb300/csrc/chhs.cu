@@ -359,12 +359,12 @@ struct Enqueue {
       }
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_pre(run, l), [&] {
         pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
-                 np1 + 1, rhs ? 1 : 0, 0, 1, to_copy);
+                 np1 + 1, rhs ? 1 : 0, 0, 1, to_copy, (const DevState*)nullptr);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_post(run, l), [&] {
         pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T)), s, Lb, C, K, np2, np2,
-                 0, 1, 0, to_state);
+                 0, 1, 0, to_state, (const DevState*)nullptr);
       });
       return;
     }
@@ -1096,7 +1096,7 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
       pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
     else
       pdl_grid(k_tile<float, true>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4),
-               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy);
+               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy, (const DevState*)nullptr);
   }
   CU(cudaGetLastError());
   CU(cudaEventRecord(ev.b, run->stream));
@@ -1581,6 +1581,31 @@ struct BatchStep {
     go(CHHS_K_FRAME, upd, kb_mixed_update, kBlock, 0, s);
   }
 
+  // A level whose own tile grid fills the GPU several times over runs as the
+  // run's own tile launch (gated), which keeps its parameters in the
+  // constant bank; a batched launch would hold them in registers and
+  // re-derive them per block (measured 35-50% slower on 512^2-1024^2 levels).
+  // The smaller levels of all runs share one batched launch.
+  static constexpr int kSoloTileBlocks = 456;  // three waves of 152 SMs at one block each
+  void go_tile(int kind, const TileJob<float>& J, int blocks, cudaStream_t s) {
+    if (!capture) return;
+    if (counter) ++*counter;
+    const dim3 grid((unsigned)J.gx, (unsigned)(blocks / J.gx));
+    timed(kind, [&] {
+      pdl_grid(k_tile<float, true>, grid, kTileThreads, tile_smem, s, J.L, J.C, J.K, J.npass, J.halo, J.rhs,
+               J.prolong, J.restrict_out, J.out, J.gate);
+    }, s);
+  }
+  void tiles(int kind, const JobList<TileJob<float>>& all, cudaStream_t s) {
+    JobList<TileJob<float>> small;
+    for (int q = 0; q < all.njobs(); ++q) {
+      const int blocks = all.start[q + 1] - all.start[q];
+      if (blocks >= kSoloTileBlocks) go_tile(kind, all.jobs[q], blocks, s);
+      else small.add(all.jobs[q], blocks);
+    }
+    go(kind, small, kb_tile<float, true>, kTileThreads, tile_smem, s);
+  }
+
   void pre(cudaStream_t s, int l, int nu1) {
     if (DIM == 2) {
       JobList<TileJob<float>> jl;
@@ -1593,7 +1618,7 @@ struct BatchStep {
         jl.add(TileJob<float>{L, r->lev32[l + 1], k32(r), to_copy, r->st, np1, np1 + 1, l > 0 ? 1 : 0, 0, 1, gx},
                gx * gy);
       }
-      go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
+      tiles(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, s);
       return;
     }
     auto runs_at = [&](auto add) {
@@ -1651,7 +1676,7 @@ struct BatchStep {
         const int gx = (L.nx + kTileW - 1) / kTileW, gy = (L.ny + kTileH - 1) / kTileH;
         jl.add(TileJob<float>{Lb, r->lev32[l + 1], k32(r), to_state, r->st, np2, np2, 0, 1, 0, gx}, gx * gy);
       }
-      go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_tile<float, true>, kTileThreads, tile_smem, s);
+      tiles(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, s);
       return;
     }
     auto runs_at = [&](auto add) {
@@ -1720,6 +1745,8 @@ struct BatchStep {
     if (st != CHHS_OK) return st;
     if (DIM == 2) {
       st = raise_to(reinterpret_cast<const void*>(kb_tile<float, true>), tile_smem);
+      if (st != CHHS_OK) return st;
+      st = raise_to(reinterpret_cast<const void*>(k_tile<float, true>), tile_smem);
       if (st != CHHS_OK) return st;
     }
     return CHHS_OK;

@@ -83,3 +83,40 @@ def test_given_start_pair_continues_the_run():
         b.step(5)
         # mu and p start cold here, so only the converged answer agrees
         assert np.max(np.abs(b.get_phi() - ref)) < 1e-9
+
+
+def _golden_sweep():
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "dt_sweep512_oracle.txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                a, b, d = line.split()
+                rows.append((float(a), float(b), float(d)))
+    return rows
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dt_halving_sweep_512(precision):
+    """Time-step halving at 512^2 (the 2D spinodal grid, h = 0.025, eps
+    0.05, gamma 1; smooth Eq. 5.1 data scaled to L = 12.8; T = 0.2, s = 0.02
+    ... 0.00125): the GPU's Cauchy differences equal the oracle's
+    (tests/golden/dt_sweep512_oracle.txt, from oracle/ only) and their ratios
+    rise towards 4, the second order of the main convergence theorem."""
+    n, L, T = 512, 12.8, 0.2
+    h = L / n
+    sols = []
+    golden = _golden_sweep()
+    dts = [g[0] for g in golden] + [golden[-1][1]]
+    for s in dts:
+        with chhs.Run((n, n), h, 0.05, 1.0, s, opts=chhs.default_opts(precision=precision, tol=1e-12)) as run:
+            run.set_phi(inputs.cosine_bump(n, L))
+            run.step(int(round(T / s)))
+            sols.append(run.get_phi())
+    d = [np.sqrt(h * h * np.sum((sols[k] - sols[k + 1]) ** 2)) for k in range(len(sols) - 1)]
+    for k, (_, _, ref) in enumerate(golden):
+        assert abs(d[k] - ref) <= 1e-6 * ref, (k, d[k], ref)
+    ratios = [d[k] / d[k + 1] for k in range(len(d) - 1)]
+    assert all(ratios[k + 1] > ratios[k] for k in range(len(ratios) - 1)), ratios
+    assert ratios[-1] > 2.8, ratios
