@@ -68,6 +68,12 @@ typedef struct {
     int coarsest_f64;  /* mixed form: 1 solves the coarsest grid of every single-precision V-cycle
                           in double precision, 0 (default) in single precision; the double form
                           always solves it in double.  Not 0 or 1: CHHS_ERR_INVALID_ARG. */
+    int f64_residual;  /* mixed form: 1 forms the defect-correction residual f - N(u) of the
+                          double-precision iterate with double-precision instructions; 0 (default)
+                          with double-single arithmetic (pairs of floats, ~48 bits) on the
+                          single-precision pipes, which run 64 times faster on GB300.  Either
+                          way the stopping norm is that of the double-precision iterate.  Not 0
+                          or 1: CHHS_ERR_INVALID_ARG. */
 } chhs_opts;
 
 /* Fill *opts with the defaults above.  Returns CHHS_ERR_INVALID_ARG on NULL. */

@@ -39,7 +39,7 @@ K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm
 class chhs_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_v", ctypes.c_int),
                 ("coarsest", ctypes.c_int), ("tol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("max_factor", ctypes.c_double), ("coarsest_f64", ctypes.c_int)]
+                ("max_factor", ctypes.c_double), ("coarsest_f64", ctypes.c_int), ("f64_residual", ctypes.c_int)]
 
 
 class chhs_request(ctypes.Structure):

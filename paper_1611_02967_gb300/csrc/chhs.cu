@@ -26,6 +26,7 @@
 #include "chhs_kernels.cuh"
 #include "chhs_tile.cuh"
 #include "chhs_corr3.cuh"
+#include "chhs_norm_df.cuh"
 #include "chhs_batch.cuh"
 
 using namespace chhs_dev;
@@ -97,7 +98,10 @@ Layout make_layout(int dim, const int n[3], int coarsest, int precision) {
   L.state_off = off;
   off += align_up(sizeof(DevState));
   int nf = L.shapes[0].n[0] * L.shapes[0].n[1] * L.shapes[0].n[2];
-  L.nparts = nblocks(nf);
+  // partial-sum slots: six per 256-cell block (the reductions), and three per
+  // block of the double-single norm (tiles of 32 x 8 cells)
+  L.nparts = (int)std::max<long long>(nblocks(nf),
+                                      (ndf_blocks(L.shapes[0].n[0], L.shapes[0].n[1], L.shapes[0].n[2]) + 1) / 2);
   L.partial_off = off;
   off += align_up(sizeof(double) * 6 * (size_t)L.nparts);
   L.phimm1_off = off;
@@ -125,7 +129,7 @@ Layout make_layout(int dim, const int n[3], int coarsest, int precision) {
 bool valid_opts(const chhs_opts& o) {
   return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.max_v >= 1 && o.coarsest >= 2 &&
          o.tol > 0 && (o.precision == 0 || o.precision == 1) && o.max_factor >= 0 &&
-         (o.coarsest_f64 == 0 || o.coarsest_f64 == 1);
+         (o.coarsest_f64 == 0 || o.coarsest_f64 == 1) && (o.f64_residual == 0 || o.f64_residual == 1);
 }
 
 bool valid_problem(int dim, const int n[3], double h, double eps, double gamma, double dt) {
@@ -500,13 +504,23 @@ struct Enqueue {
     return CHHS_OK;
   }
 
+  // The finest level's scalars for the double-single residual.
+  static DfCoefs df_coefs(const chhs_t* run) {
+    const Level<double>& L = run->lev[0];
+    return DfCoefs{df_from_double_host(L.sih2), df_from_double_host(L.ih2), df_from_double_host(L.e34ih2),
+                   df_from_double_host(run->gamma), (float)run->dt};
+  }
+
   // The stopping norm (and, when mixed, the next inner solve's right-hand side).
   static void norm(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int mode, int use_cond) {
     const Coefs<double> K = coefs<double>(run);
     const Level<double>& L = run->lev[0];
     const int nb = run->norm_blocks;
     launch(run, s, CHHS_K_NORM, L.ncell, [&] {
-      if (mixed(run))
+      if (mixed(run) && !run->opts.f64_residual)
+        pdl(k_norm_mixed_df<DIM>, (int)ndf_blocks(L.nx, L.ny, L.nz), kNdfTX * kNdfTY, s, L, df_coefs(run),
+            run->lev32[0], run->partials, run->st, cond, mode, use_cond);
+      else if (mixed(run))
         pdl(k_norm_mixed<DIM>, nb, kBlock, s, L, K, run->lev32[0], run->partials, run->st, cond, mode, use_cond);
       else
         pdl(k_norm<double, DIM>, nb, kBlock, s, L, K, run->partials, run->st, cond, mode, use_cond);
@@ -891,6 +905,7 @@ chhs_status chhs_default_opts(chhs_opts* o) {
   o->precision = 0;
   o->max_factor = 50.0;
   o->coarsest_f64 = 0;
+  o->f64_residual = 0;
   return CHHS_OK;
 }
 
@@ -1561,9 +1576,16 @@ struct BatchStep {
 
   void norm(cudaStream_t s, cudaGraphConditionalHandle cond, int mode) {
     JobList<NormJob> jl;
-    for (chhs_t* r : b->runs)
-      jl.add(NormJob{r->lev[0], r->lev32[0], k64(r), r->partials, r->st}, r->norm_blocks);
-    go(CHHS_K_NORM, jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cond, mode, b->d_ticket + 1);
+    const bool df = !b->opts.f64_residual;
+    for (chhs_t* r : b->runs) {
+      const Level<double>& L = r->lev[0];
+      jl.add(NormJob{L, r->lev32[0], k64(r), Enqueue<DIM>::df_coefs(r), r->partials, r->st},
+             df ? (int)ndf_blocks(L.nx, L.ny, L.nz) : r->norm_blocks);
+    }
+    if (df)
+      go(CHHS_K_NORM, jl, kb_norm_mixed_df<DIM>, kNdfTX * kNdfTY, 0, s, b->d_ticket, cond, mode, b->d_ticket + 1);
+    else
+      go(CHHS_K_NORM, jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cond, mode, b->d_ticket + 1);
   }
 
   void vcycle(cudaStream_t s) {
@@ -1586,7 +1608,7 @@ struct BatchStep {
   // constant bank; a batched launch would hold them in registers and
   // re-derive them per block (measured 35-50% slower on 512^2-1024^2 levels).
   // The smaller levels of all runs share one batched launch.
-  static constexpr int kSoloTileBlocks = 456;  // three waves of 152 SMs at one block each
+  static constexpr int kSoloTileBlocks = 128;  // a level of 512 x 256 cells or more
   void go_tile(int kind, const TileJob<float>& J, int blocks, cudaStream_t s) {
     if (!capture) return;
     if (counter) ++*counter;
@@ -1596,14 +1618,37 @@ struct BatchStep {
                J.prolong, J.restrict_out, J.out, J.gate);
     }, s);
   }
+  // Side streams of the capture: the big per-run tile launches of one phase
+  // run on parallel branches of the graph (one run's wave tail overlaps the
+  // next run's blocks), the batched launch of the small levels beside them.
+  static constexpr int kBranches = 8;
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kBranches] = {};
+
   void tiles(int kind, const JobList<TileJob<float>>& all, cudaStream_t s) {
     JobList<TileJob<float>> small;
+    std::vector<int> big;
     for (int q = 0; q < all.njobs(); ++q) {
       const int blocks = all.start[q + 1] - all.start[q];
-      if (blocks >= kSoloTileBlocks) go_tile(kind, all.jobs[q], blocks, s);
+      if (blocks >= kSoloTileBlocks) big.push_back(q);
       else small.add(all.jobs[q], blocks);
     }
+    const bool fan = capture && branch[0] && big.size() > 1;
+    const int nb = fan ? std::min<int>(kBranches, (int)big.size()) : 0;
+    if (fan) {
+      cudaEventRecord(fork_ev, s);
+      for (int q = 0; q < nb; ++q) cudaStreamWaitEvent(branch[q], fork_ev, 0);
+    }
+    for (size_t q = 0; q < big.size(); ++q) {
+      const int jq = big[q];
+      go_tile(kind, all.jobs[jq], all.start[jq + 1] - all.start[jq], fan ? branch[q % nb] : s);
+    }
     go(kind, small, kb_tile<float, true>, kTileThreads, tile_smem, s);
+    if (fan)
+      for (int q = 0; q < nb; ++q) {
+        cudaEventRecord(join_ev[q], branch[q]);
+        cudaStreamWaitEvent(s, join_ev[q], 0);
+      }
   }
 
   void pre(cudaStream_t s, int l, int nu1) {
@@ -1762,8 +1807,8 @@ struct BatchStep {
     capture = true;
     cur = 0;
     struct CaptureRes {
-      cudaStream_t s[3] = {nullptr, nullptr, nullptr};
-      cudaEvent_t e[2] = {nullptr, nullptr};
+      cudaStream_t s[3 + kBranches] = {};
+      cudaEvent_t e[3 + kBranches] = {};
       ~CaptureRes() {
         for (int q : {1, 0}) {
           cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -1780,9 +1825,14 @@ struct BatchStep {
         cudaGetLastError();
       }
     } res;
-    for (int q = 0; q < 3; ++q) BCU(cudaStreamCreateWithFlags(&res.s[q], cudaStreamNonBlocking));
-    for (int q = 0; q < 2; ++q) BCU(cudaEventCreateWithFlags(&res.e[q], cudaEventDisableTiming));
+    for (int q = 0; q < 3 + kBranches; ++q) BCU(cudaStreamCreateWithFlags(&res.s[q], cudaStreamNonBlocking));
+    for (int q = 0; q < 3 + kBranches; ++q) BCU(cudaEventCreateWithFlags(&res.e[q], cudaEventDisableTiming));
     cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2];
+    for (int q = 0; q < kBranches; ++q) {
+      branch[q] = res.s[3 + q];
+      join_ev[q] = res.e[3 + q];
+    }
+    fork_ev = res.e[2];
     int n_frame = 0, n_v = 0;
     BCU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     counter = &n_frame;
@@ -1819,6 +1869,7 @@ struct BatchStep {
     advance(cs);
     counter = nullptr;
     BCU(cudaStreamEndCapture(cs, &b->graph));
+    for (int q = 0; q < kBranches; ++q) branch[q] = nullptr;
     BCU(cudaGraphInstantiate(&b->exec, b->graph, 0));
     b->launches_per_v = n_v;
     b->launches_per_step = n_frame;

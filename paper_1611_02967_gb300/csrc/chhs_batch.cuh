@@ -12,6 +12,7 @@
 #pragma once
 #include "chhs_corr3.cuh"
 #include "chhs_kernels.cuh"
+#include "chhs_norm_df.cuh"
 #include "chhs_tile.cuh"
 
 namespace chhs_dev {
@@ -98,26 +99,18 @@ struct NormJob {
   Level<double> L;
   Level<float> G;
   Coefs<double> K;
+  DfCoefs Kdf;
   double* partials;
   DevState* st;
 };
 
-// The stopping norms of all runs (mode 0: start of a step, every run; mode 1:
-// after a V-cycle, the runs still iterating).  Each run's last block takes
-// that run's decision; the last block of the launch then sets the loop
-// condition to "any run still iterating".
-template <int DIM>
-__global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, const int* start, int njobs,
-                                                        unsigned int* ticket, cudaGraphConditionalHandle cond,
-                                                        int mode, unsigned int* any_out) {
-  pdl_enter();
+// The last block of a batched norm launch: after every run's own last block
+// has taken its decision, the loop condition is set to "any run still
+// iterating" (and written to any_out for the host-driven profiling path).
+__device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njobs, unsigned int* ticket,
+                                                    cudaGraphConditionalHandle cond, unsigned int* any_out) {
   __shared__ bool last_all;
   __shared__ int any_go;
-  const int j = job_of(start, njobs, blockIdx.x);
-  const NormJob& J = job_in_smem(jobs, j);
-  if (mode == 0 || gate_open(J.st))
-    norm_mixed_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode,
-                         0);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -136,6 +129,37 @@ __global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, con
     *any_out = any_go ? 1u : 0u;
     if (cond) cudaGraphSetConditional(cond, any_go ? 1u : 0u);
   }
+}
+
+// The stopping norms of all runs (mode 0: start of a step, every run; mode 1:
+// after a V-cycle, the runs still iterating).  Each run's last block takes
+// that run's decision.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, const int* start, int njobs,
+                                                        unsigned int* ticket, cudaGraphConditionalHandle cond,
+                                                        int mode, unsigned int* any_out) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const NormJob& J = job_in_smem(jobs, j);
+  if (mode == 0 || gate_open(J.st))
+    norm_mixed_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode,
+                         0);
+  batch_norm_epilogue(jobs, njobs, ticket, cond, any_out);
+}
+
+// The same with the double-single residual (chhs_norm_df.cuh).
+template <int DIM>
+__global__ void __launch_bounds__(kNdfTX * kNdfTY) kb_norm_mixed_df(const NormJob* jobs, const int* start, int njobs,
+                                                                  unsigned int* ticket,
+                                                                  cudaGraphConditionalHandle cond, int mode,
+                                                                  unsigned int* any_out) {
+  pdl_enter();
+  const int j = job_of(start, njobs, blockIdx.x);
+  const NormJob& J = job_in_smem(jobs, j);
+  if (mode == 0 || gate_open(J.st))
+    norm_mixed_df_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.Kdf, J.G, J.partials, J.st, 0,
+                            mode, 0);
+  batch_norm_epilogue(jobs, njobs, ticket, cond, any_out);
 }
 
 template <typename T>

@@ -405,3 +405,31 @@ def test_mixed_form_double_precision_coarsest_solve(shape, h, eps, gamma, dt):
             vs.append(v)
     assert np.max(np.abs(phis[0] - phis[1])) <= PHI_TOL[1]
     assert vs[0] == vs[1], vs
+
+
+@pytest.mark.parametrize("shape,h,eps,gamma,dt", [((256, 256), 0.025, 0.02, 4.0, 0.005),
+                                                  ((32, 32, 32), 0.05, 0.02, 4.0, 0.005),
+                                                  ((24, 40), 0.1, 0.08, 0.0, 0.01)])
+def test_mixed_residual_double_single_and_double_agree(shape, h, eps, gamma, dt):
+    """The mixed form's defect-correction residual in double-single
+    arithmetic (the default) and in double precision (f64_residual = 1)
+    drive the same iteration: equal V-cycle counts, steps within the
+    mixed-precision bound of each other, and a reported stopping norm that
+    equals the oracle's double-precision residual norm of the GPU's own
+    fields."""
+    phi0 = inputs.spinodal(shape, 45, mean=-0.05, amplitude=0.3)
+    prm = oracle.Params(h, eps, gamma, dt)
+    phis, vs = [], []
+    for f64 in (0, 1):
+        with _run(shape, h, eps, gamma, dt, 1, f64_residual=f64) as run:
+            run.set_phi(phi0)
+            _, v, _ = run.step(3)
+            phim, phimm1, _, _ = run.get_state()
+            _, _, r = run.step(1)
+            phi, _, mu, p = run.get_state()
+            nrm = oracle.residual(phim, phimm1, phi, mu, p, prm)[3]
+            assert abs(r - nrm) <= 1e-3 * nrm + 1e-14, (f64, r, nrm)
+            phis.append(phi)
+            vs.append(v)
+    assert vs[0] == vs[1], vs
+    assert np.max(np.abs(phis[0] - phis[1])) <= PHI_TOL[1]
