@@ -209,6 +209,7 @@ typedef struct {
   int tile_threads;   /* threads per tile in the 2D mixed form */
   int coarse_nu1;     /* pre- and post-smoothing sweeps on the levels below the finest (the finest */
   int coarse_nu2;     /* keeps opts->nu1, nu2) */
+  int tile_w, tile_h; /* interior of a tile in the 2D mixed form (even; default 32 x 16) */
   double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
                          the setting in force was timed (every candidate failed, or the fastest
                          could not be rebuilt and the original setting was kept) */
@@ -217,8 +218,9 @@ typedef struct {
 /* Autotuner of the handle's launch shapes and coarse sweep counts: tries
  * candidate settings (where the one-block tail starts; in double precision,
  * up to which level size the split update is used; in the 2D mixed form, the
- * tile block size; the sweeps on the levels below the finest: the options'
- * nu1, nu2 or, when both exceed 1, one each), times
+ * tile block size and tile shape, 32 x 16, 32 x 32 or 64 x 16 cells; the
+ * sweeps on the levels below the finest: the options' nu1, nu2 or, when both
+ * exceed 1, one each), times
  * trial_steps steps of the handle's own problem from its current state with
  * each, keeps the fastest and rebuilds the step graph with it.  The state is
  * restored after every trial and at the end, so the run continues exactly
@@ -235,8 +237,9 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out);
  * the same shape) and rebuild the step graph; ms_per_step is ignored.  The
  * state is kept.  Errors: CHHS_ERR_INVALID_ARG (NULL, steps pending, a run
  * of a batch, tail_cells < 1, split_threads < 0, tile_threads not a multiple
- * of 32 in 32..1024, coarse sweep counts < 0 or both 0, or a setting the
- * grid cannot take -- the previous tuning is then kept), CHHS_ERR_CUDA. */
+ * of 32 in 32..1024, coarse sweep counts < 0 or both 0, tile sides odd or
+ * below 2, tiles over 4096 cells, or a setting the grid cannot take -- the
+ * previous tuning is then kept), CHHS_ERR_CUDA. */
 chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* tuning);
 
 /* Discrete mass (phi^m, 1) = h^d sum phi^m (Section 4, mass conservation). */

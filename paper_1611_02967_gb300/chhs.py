@@ -56,7 +56,8 @@ class chhs_run_desc(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """chhs_tuning (include/chhs.h)."""
     _fields_ = [("tail_cells", ctypes.c_int), ("split_threads", ctypes.c_int), ("tile_threads", ctypes.c_int),
-                ("coarse_nu1", ctypes.c_int), ("coarse_nu2", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("coarse_nu1", ctypes.c_int), ("coarse_nu2", ctypes.c_int), ("tile_w", ctypes.c_int),
+                ("tile_h", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
 
 
 class ChhsError(RuntimeError):
@@ -323,11 +324,13 @@ class Run:
         t = Tuning()
         self._check(lib().chhs_autotune(self.handle, int(trial_steps), ctypes.byref(t)))
         return dict(tail_cells=t.tail_cells, split_threads=t.split_threads, tile_threads=t.tile_threads,
-                    coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2, ms_per_step=t.ms_per_step)
+                    coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2, tile_w=t.tile_w, tile_h=t.tile_h,
+                    ms_per_step=t.ms_per_step)
 
-    def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2):
+    def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2, tile_w=32, tile_h=16):
         """chhs_set_tuning: apply launch shapes and coarse sweep counts."""
-        t = Tuning(int(tail_cells), int(split_threads), int(tile_threads), int(coarse_nu1), int(coarse_nu2), 0.0)
+        t = Tuning(int(tail_cells), int(split_threads), int(tile_threads), int(coarse_nu1), int(coarse_nu2),
+                   int(tile_w), int(tile_h), 0.0)
         self._check(lib().chhs_set_tuning(self.handle, ctypes.byref(t)))
 
     def mass(self):

@@ -186,6 +186,7 @@ struct chhs {
   int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kTileThreads;
   int norm_blocks = 1;              // grid of the stopping-norm kernels (whole blocks per SM)
   int nu1c = 2, nu2c = 2;           // sweeps on the levels below the finest (chhs_autotune; opts by default)
+  int tile_w = kTileW, tile_h = kTileH;  // tile interior of the 2D single-precision levels (chhs_autotune)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
@@ -339,7 +340,8 @@ struct Enqueue {
     if constexpr (use_tiles<T>()) {
       // 2D single precision: pre-smoothing (+ right-hand side) + residual +
       // restriction in one tiled launch, prolongation + post-smoothing in another
-      const dim3 grid((L.nx + kTileW - 1) / kTileW, (L.ny + kTileH - 1) / kTileH);
+      const int tw = run->tile_w, th = run->tile_h;
+      const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
       const int nf = tile_nfields<CORR>();
       const int np1 = 2 * nu_pre(run, l), np2 = 2 * nu_post(run, l);
       // the pre-smoothing launch writes the second copy of the state (and the
@@ -362,13 +364,13 @@ struct Enqueue {
         to_state.p64 = run->lev[0].p;
       }
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_pre(run, l), [&] {
-        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T)), s, L, C, K, np1,
-                 np1 + 1, rhs ? 1 : 0, 0, 1, to_copy, (const DevState*)nullptr);
+        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T), tw, th), s, L, C,
+                 K, np1, np1 + 1, rhs ? 1 : 0, 0, 1, to_copy, (const DevState*)nullptr, tw, th);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_post(run, l), [&] {
-        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T)), s, Lb, C, K, np2, np2,
-                 0, 1, 0, to_state, (const DevState*)nullptr);
+        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T), tw, th), s, Lb, C, K,
+                 np2, np2, 0, 1, 0, to_state, (const DevState*)nullptr, tw, th);
       });
       return;
     }
@@ -495,7 +497,7 @@ struct Enqueue {
     CU(raise_to(ktail, smem));
     if constexpr (use_tiles<T>()) {
       const int halo = 2 * std::max(std::max(run->opts.nu1, run->opts.nu2), std::max(run->nu1c, run->nu2c)) + 1;
-      const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T));
+      const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->tile_w, run->tile_h);
       const void* ktile = reinterpret_cast<const void*>(k_tile<T, CORR>);
       if (!fits(ktile, tb))
         return fail(run, CHHS_ERR_INVALID_ARG, "nu1/nu2 too large for the single-precision tiles");
@@ -1104,14 +1106,15 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
   const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
   const int np1 = 2 * run->opts.nu1;
   const TileOut<float> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3, nullptr, nullptr, nullptr};
-  const dim3 grid((L.nx + kTileW - 1) / kTileW, (L.ny + kTileH - 1) / kTileH);
+  const int tw = run->tile_w, th = run->tile_h;
+  const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
   for (int k = 0; k <= npasses; ++k) {
     if (k == 1) CU(cudaEventRecord(ev.a, run->stream));
     if (run->dim == 3)
       pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
     else
-      pdl_grid(k_tile<float, true>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4),
-               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy, (const DevState*)nullptr);
+      pdl_grid(k_tile<float, true>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4, tw, th),
+               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy, (const DevState*)nullptr, tw, th);
   }
   CU(cudaGetLastError());
   CU(cudaEventRecord(ev.b, run->stream));
@@ -1170,12 +1173,14 @@ chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
   if (t->tail_cells < 1 || t->split_threads < 0 || t->tile_threads < 32 || t->tile_threads > 1024 ||
-      t->tile_threads % 32 != 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 || t->coarse_nu1 + t->coarse_nu2 < 1)
+      t->tile_threads % 32 != 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 || t->coarse_nu1 + t->coarse_nu2 < 1 ||
+      t->tile_w < 2 || t->tile_h < 2 || t->tile_w % 2 != 0 || t->tile_h % 2 != 0 || t->tile_w * t->tile_h > 4096)
     return fail(run, CHHS_ERR_INVALID_ARG, "invalid tuning");
   run->err.clear();
   CU(cudaStreamSynchronize(run->stream));
-  const int keep[5] = {run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c};
-  auto rebuild = [&](int tc, int sp, int tt, int n1, int n2) -> chhs_status {
+  const int keep[7] = {run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c, run->tile_w,
+                       run->tile_h};
+  auto rebuild = [&](int tc, int sp, int tt, int n1, int n2, int tw, int th) -> chhs_status {
     if (run->exec) cudaGraphExecDestroy(run->exec);
     if (run->graph) cudaGraphDestroy(run->graph);
     run->exec = nullptr;
@@ -1185,13 +1190,16 @@ chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
     run->tile_threads = tt;
     run->nu1c = n1;
     run->nu2c = n2;
+    run->tile_w = tw;
+    run->tile_h = th;
     place_tail(run);
     return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
   };
-  chhs_status s = rebuild(t->tail_cells, t->split_threads, t->tile_threads, t->coarse_nu1, t->coarse_nu2);
+  chhs_status s = rebuild(t->tail_cells, t->split_threads, t->tile_threads, t->coarse_nu1, t->coarse_nu2, t->tile_w,
+                          t->tile_h);
   if (s != CHHS_OK) {
     const std::string why = run->err;
-    if (rebuild(keep[0], keep[1], keep[2], keep[3], keep[4]) != CHHS_OK)
+    if (rebuild(keep[0], keep[1], keep[2], keep[3], keep[4], keep[5], keep[6]) != CHHS_OK)
       return fail(run, CHHS_ERR_CUDA, "could not rebuild the step graph");
     return fail(run, s, why.empty() ? "tuning refused" : why);
   }
@@ -1204,7 +1212,7 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   run->err.clear();
   struct Cand {
-    int tail_cells, split_threads, tile_threads, nu1c, nu2c;
+    int tail_cells, split_threads, tile_threads, nu1c, nu2c, tile_w, tile_h;
   };
   std::vector<Cand> cands;
   const bool mixed = run->opts.precision == 1;
@@ -1213,16 +1221,24 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   // latency-bound levels; the V-cycle counts the trials measure decide)
   std::vector<std::pair<int, int>> coarse = {{run->opts.nu1, run->opts.nu2}};
   if (run->opts.nu1 > 1 && run->opts.nu2 > 1) coarse.push_back({1, 1});
+  // 2D mixed form: tile shapes (interior cells; wider tiles recompute a
+  // smaller share of halo cells but make fewer blocks) and block sizes
+  struct Shape2 {
+    int tt, tw, th;
+  };
+  const Shape2 shapes[4] = {{256, 32, 16}, {512, 32, 16}, {512, 32, 32}, {512, 64, 16}};
   for (const auto& cn : coarse) {
     if (!mixed) {
       const int tails[2] = {64, run->dim == 2 ? 256 : 512};
       for (int tc : tails)
-        for (int sp : {0, 8192, 32768}) cands.push_back({tc, sp, run->tile_threads, cn.first, cn.second});
+        for (int sp : {0, 8192, 32768})
+          cands.push_back({tc, sp, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h});
     } else if (run->dim == 2) {
       for (int tc : {256, 1024, 2048})
-        for (int tt : {256, 512}) cands.push_back({tc, run->split_threads, tt, cn.first, cn.second});
+        for (const Shape2& sh : shapes) cands.push_back({tc, run->split_threads, sh.tt, cn.first, cn.second, sh.tw, sh.th});
     } else {
-      for (int tc : {64, 512}) cands.push_back({tc, run->split_threads, run->tile_threads, cn.first, cn.second});
+      for (int tc : {64, 512})
+        cands.push_back({tc, run->split_threads, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h});
     }
   }
   // the run's state (phi^m, phi^{m-1}, mu, p), restored before every trial and at the end
@@ -1265,10 +1281,13 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     run->tile_threads = c.tile_threads;
     run->nu1c = c.nu1c;
     run->nu2c = c.nu2c;
+    run->tile_w = c.tile_w;
+    run->tile_h = c.tile_h;
     place_tail(run);
     return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
   };
-  const Cand orig{run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c};
+  const Cand orig{run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c, run->tile_w,
+                  run->tile_h};
   Cand best = orig;
   float best_ms = -1.f;
   chhs_status s;
@@ -1303,6 +1322,8 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     out->tile_threads = run->tile_threads;
     out->coarse_nu1 = run->nu1c;
     out->coarse_nu2 = run->nu2c;
+    out->tile_w = run->tile_w;
+    out->tile_h = run->tile_h;
     out->ms_per_step = best_ms < 0.f ? -1.0 : (double)best_ms / trial_steps;
   }
   return CHHS_OK;
@@ -1615,7 +1636,7 @@ struct BatchStep {
     const dim3 grid((unsigned)J.gx, (unsigned)(blocks / J.gx));
     timed(kind, [&] {
       pdl_grid(k_tile<float, true>, grid, kTileThreads, tile_smem, s, J.L, J.C, J.K, J.npass, J.halo, J.rhs,
-               J.prolong, J.restrict_out, J.out, J.gate);
+               J.prolong, J.restrict_out, J.out, J.gate, (int)kTileW, (int)kTileH);
     }, s);
   }
   // Side streams of the capture: the big per-run tile launches of one phase

@@ -34,14 +34,16 @@
 
 namespace chhs_dev {
 
-constexpr int kTileW = 32, kTileH = 16;  // tile interior (even, so restriction stays inside)
+constexpr int kTileW = 32, kTileH = 16;  // default tile interior (even, so restriction stays inside);
+                                         // chhs_autotune may pick 32 x 32 or 64 x 16
 constexpr int kTileThreads = 512;
 
 template <bool CORR>
 __host__ __device__ constexpr int tile_nfields() { return CORR ? 9 : 8; }
 
-__host__ __device__ inline size_t tile_smem_bytes(int halo, int nfields, size_t elem) {
-  return (size_t)(kTileW + 2 * halo) * (kTileH + 2 * halo) * nfields * elem;
+__host__ __device__ inline size_t tile_smem_bytes(int halo, int nfields, size_t elem, int tw = kTileW,
+                                                  int th = kTileH) {
+  return (size_t)(tw + 2 * halo) * (th + 2 * halo) * nfields * elem;
 }
 
 // Coefficients of cell (i, j) from phi* in shared memory: face values a_f,
@@ -129,13 +131,14 @@ __device__ __forceinline__ void tile_N(const TileView<T, CORR>& V, int s, int SW
 template <typename T, bool CORR>
 __device__ __forceinline__ void tile_body(int bx, int by, const Level<T>& L, const Level<T>& Cl,
                                           const Coefs<T>& K, int npass, int halo, int rhs, int prolong,
-                                          int restrict_out, const TileOut<T>& out) {
+                                          int restrict_out, const TileOut<T>& out, int tw = kTileW,
+                                          int th = kTileH) {
   // The tiles serve the correction-form (single-precision) levels only: the
   // plain form's right-hand side f_mu carries the shift of cubic_P, which
   // tile_N does not.
   static_assert(CORR, "k_tile runs the correction form only");
   extern __shared__ __align__(16) unsigned char tile_smem[];
-  const int SW = kTileW + 2 * halo, SH = kTileH + 2 * halo, SN = SW * SH;
+  const int SW = tw + 2 * halo, SH = th + 2 * halo, SN = SW * SH;
   TileView<T, CORR> V;
   {
     T* base = reinterpret_cast<T*>(tile_smem);
@@ -144,7 +147,7 @@ __device__ __forceinline__ void tile_body(int bx, int by, const Level<T>& L, con
     V.phib = CORR ? base + 8 * SN : nullptr;
   }
   const int nx = L.nx, ny = L.ny;
-  const int tx0 = bx * kTileW, ty0 = by * kTileH;  // tile origin (global)
+  const int tx0 = bx * tw, ty0 = by * th;  // tile origin (global)
   const int gx0 = tx0 - halo, gy0 = ty0 - halo;                      // shared-memory origin (global)
 
   // load the tile and its halo (cells outside the domain are never read);
@@ -177,9 +180,9 @@ __device__ __forceinline__ void tile_body(int bx, int by, const Level<T>& L, con
   // the cells of region "tile grown by g" inside the domain: [x0, x1) x [y0, y1)
   auto region = [&](int g, int& x0, int& x1, int& y0, int& y1) {
     x0 = max(tx0 - g, 0);
-    x1 = min(tx0 + kTileW + g, nx);
+    x1 = min(tx0 + tw + g, nx);
     y0 = max(ty0 - g, 0);
-    y1 = min(ty0 + kTileH + g, ny);
+    y1 = min(ty0 + th + g, ny);
   };
 
   if (rhs) {  // f += N(R u) wherever pass 1 needs f
@@ -266,7 +269,7 @@ __device__ __forceinline__ void tile_body(int bx, int by, const Level<T>& L, con
     // summed by shuffles in a fixed order; the round count is uniform so
     // every thread takes part in the shuffles
     constexpr int NV = CORR ? 7 : 6;
-    const int cw = kTileW / 2, chh = kTileH / 2, total = 4 * cw * chh;
+    const int cw = tw / 2, chh = th / 2, total = 4 * cw * chh;
     for (int r = 0; r < total; r += blockDim.x) {
       const int t = r + threadIdx.x, qq = t >> 2, d = t & 3;
       const int I = (tx0 >> 1) + qq % cw, J = (ty0 >> 1) + qq / cw;
@@ -313,10 +316,11 @@ template <typename T, bool CORR>
 __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Level<T> L,
                                                       const __grid_constant__ Level<T> Cl, Coefs<T> K, int npass,
                                                       int halo, int rhs, int prolong, int restrict_out,
-                                                      const __grid_constant__ TileOut<T> out, const DevState* gate) {
+                                                      const __grid_constant__ TileOut<T> out, const DevState* gate,
+                                                      int tw, int th) {
   pdl_enter();
   if (gate && *(volatile const int*)&gate->go == 0) return;
-  tile_body<T, CORR>(blockIdx.x, blockIdx.y, L, Cl, K, npass, halo, rhs, prolong, restrict_out, out);
+  tile_body<T, CORR>(blockIdx.x, blockIdx.y, L, Cl, K, npass, halo, rhs, prolong, restrict_out, out, tw, th);
 }
 
 }  // namespace chhs_dev

@@ -28,6 +28,7 @@ def test_autotune_keeps_state_and_steps_match_oracle(shape, precision):
             assert t["tail_cells"] in (64, 256, 512) and t["split_threads"] in (0, 8192, 32768)
         elif len(shape) == 2:
             assert t["tail_cells"] in (256, 1024, 2048) and t["tile_threads"] in (256, 512)
+            assert (t["tile_w"], t["tile_h"]) in ((32, 16), (32, 32), (64, 16))
         else:
             assert t["tail_cells"] in (64, 512)
         assert (t["coarse_nu1"], t["coarse_nu2"]) in ((2, 2), (1, 1))
@@ -38,10 +39,10 @@ def test_autotune_keeps_state_and_steps_match_oracle(shape, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("shape", [(256, 256), (32, 32, 32)])
 def test_one_coarse_sweep_reaches_the_same_answer(shape, precision):
-    """The coarse sweep counts the autotuner may choose change only the path
-    to the solution: with one sweep each way below the finest level
-    (chhs_set_tuning) the steps still equal the oracle's, and the state is
-    kept across the rebuild."""
+    """The coarse sweep counts and tile shapes the autotuner may choose change
+    only the path to the solution: with one sweep each way below the finest
+    level and 64 x 16 or 32 x 32 tiles (chhs_set_tuning) the steps still
+    equal the oracle's, and the state is kept across the rebuild."""
     h, eps, gamma, dt = (0.025, 0.05, 1.0, 0.005) if len(shape) == 2 else (0.05, 0.04, 2.0, 0.005)
     phi0 = inputs.spinodal(shape, 43, mean=0.0, amplitude=0.05)
     with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=precision)) as run:
@@ -49,11 +50,12 @@ def test_one_coarse_sweep_reaches_the_same_answer(shape, precision):
         run.step(2)
         before = run.get_state()
         t = run.autotune(2)
-        run.set_tuning(t["tail_cells"], t["split_threads"], t["tile_threads"], 1, 1)
-        for a, b in zip(before, run.get_state()):
-            assert np.array_equal(a, b)
-        for _ in range(2):
+        for tw, th in ((64, 16), (32, 32)):
+            run.set_tuning(t["tail_cells"], t["split_threads"], t["tile_threads"], 1, 1, tw, th)
+            for a, b in zip(before, run.get_state()):
+                assert np.array_equal(a, b)
             _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+            run.set_state(*before)
         with pytest.raises(chhs.ChhsError):
             run.set_tuning(t["tail_cells"], t["split_threads"], 100, 1, 1)  # not a multiple of 32
         _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
