@@ -210,6 +210,9 @@ typedef struct {
   int coarse_nu1;     /* pre- and post-smoothing sweeps on the levels below the finest (the finest */
   int coarse_nu2;     /* keeps opts->nu1, nu2) */
   int tile_w, tile_h; /* interior of a tile in the 2D mixed form (even; default 32 x 16) */
+  int norm_f64_per8;  /* mixed form, double-single residual: of every 8 tiles of the residual
+                         kernel, how many use double-precision instructions (0..8; default 3), so
+                         that the FP64 pipe works beside the single-precision ones */
   double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
                          the setting in force was timed (every candidate failed, or the fastest
                          could not be rebuilt and the original setting was kept) */
@@ -238,7 +241,8 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out);
  * state is kept.  Errors: CHHS_ERR_INVALID_ARG (NULL, steps pending, a run
  * of a batch, tail_cells < 1, split_threads < 0, tile_threads not a multiple
  * of 32 in 32..1024, coarse sweep counts < 0 or both 0, tile sides odd or
- * below 2, tiles over 4096 cells, or a setting the grid cannot take -- the
+ * below 2, tiles over 4096 cells, norm_f64_per8 outside 0..8, or a setting
+ * the grid cannot take -- the
  * previous tuning is then kept), CHHS_ERR_CUDA. */
 chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* tuning);
 

@@ -68,6 +68,11 @@ int level_fields(int dim, bool single) {
   return kBaseFields + (dim == 3 ? 14 : 12) + (single ? 1 + (dim == 2 ? 6 : 0) : 0);
 }
 
+// The mixed form's residual kernel: of every 8 tiles, this many are evaluated
+// with double-precision instructions and the rest in double-single
+// arithmetic, so that both kinds of pipes are busy (chhs_norm_df.cuh).
+constexpr int kNormF64Per8 = 3;
+
 // Levels with at most this many cells run inside the one-block tail kernel.
 // In double precision one SM does 2 FMA per clock and a single warp's
 // dependent FP64 chain is slow, so only the tiniest levels (8 x 8, 4 x 4 x 4)
@@ -187,6 +192,7 @@ struct chhs {
   int norm_blocks = 1;              // grid of the stopping-norm kernels (whole blocks per SM)
   int nu1c = 2, nu2c = 2;           // sweeps on the levels below the finest (chhs_autotune; opts by default)
   int tile_w = kTileW, tile_h = kTileH;  // tile interior of the 2D single-precision levels (chhs_autotune)
+  int norm_f64_per8 = kNormF64Per8;      // blocks of 8 whose residual runs on the FP64 pipe (mixed form)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
@@ -520,8 +526,8 @@ struct Enqueue {
     const int nb = run->norm_blocks;
     launch(run, s, CHHS_K_NORM, L.ncell, [&] {
       if (mixed(run) && !run->opts.f64_residual)
-        pdl(k_norm_mixed_df<DIM>, (int)ndf_blocks(L.nx, L.ny, L.nz), kNdfTX * kNdfTY, s, L, df_coefs(run),
-            run->lev32[0], run->partials, run->st, cond, mode, use_cond);
+        pdl(k_norm_mixed_df<DIM>, (int)ndf_blocks(L.nx, L.ny, L.nz), kNdfTX * kNdfTY, s, L, df_coefs(run), K,
+            run->norm_f64_per8, run->lev32[0], run->partials, run->st, cond, mode, use_cond);
       else if (mixed(run))
         pdl(k_norm_mixed<DIM>, nb, kBlock, s, L, K, run->lev32[0], run->partials, run->st, cond, mode, use_cond);
       else
@@ -1174,8 +1180,10 @@ chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
   if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
   if (t->tail_cells < 1 || t->split_threads < 0 || t->tile_threads < 32 || t->tile_threads > 1024 ||
       t->tile_threads % 32 != 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 || t->coarse_nu1 + t->coarse_nu2 < 1 ||
-      t->tile_w < 2 || t->tile_h < 2 || t->tile_w % 2 != 0 || t->tile_h % 2 != 0 || t->tile_w * t->tile_h > 4096)
+      t->tile_w < 2 || t->tile_h < 2 || t->tile_w % 2 != 0 || t->tile_h % 2 != 0 || t->tile_w * t->tile_h > 4096 ||
+      t->norm_f64_per8 < 0 || t->norm_f64_per8 > 8)
     return fail(run, CHHS_ERR_INVALID_ARG, "invalid tuning");
+  run->norm_f64_per8 = t->norm_f64_per8;
   run->err.clear();
   CU(cudaStreamSynchronize(run->stream));
   const int keep[7] = {run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c, run->tile_w,
@@ -1324,6 +1332,7 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     out->coarse_nu2 = run->nu2c;
     out->tile_w = run->tile_w;
     out->tile_h = run->tile_h;
+    out->norm_f64_per8 = run->norm_f64_per8;
     out->ms_per_step = best_ms < 0.f ? -1.0 : (double)best_ms / trial_steps;
   }
   return CHHS_OK;
@@ -1600,7 +1609,7 @@ struct BatchStep {
     const bool df = !b->opts.f64_residual;
     for (chhs_t* r : b->runs) {
       const Level<double>& L = r->lev[0];
-      jl.add(NormJob{L, r->lev32[0], k64(r), Enqueue<DIM>::df_coefs(r), r->partials, r->st},
+      jl.add(NormJob{L, r->lev32[0], k64(r), Enqueue<DIM>::df_coefs(r), r->partials, r->st, r->norm_f64_per8},
              df ? (int)ndf_blocks(L.nx, L.ny, L.nz) : r->norm_blocks);
     }
     if (df)

@@ -102,23 +102,31 @@ struct NormJob {
   DfCoefs Kdf;
   double* partials;
   DevState* st;
+  int f64_per8;
 };
 
-// The last block of a batched norm launch: after every run's own last block
-// has taken its decision, the loop condition is set to "any run still
-// iterating" (and written to any_out for the host-driven profiling path).
-__device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njobs, unsigned int* ticket,
-                                                    cudaGraphConditionalHandle cond, unsigned int* any_out) {
-  __shared__ bool last_all;
+// The end of a batched norm launch: every run reports once -- from its last
+// block after that block has taken the run's loop decision, or from its
+// block 0 when the run is not iterating and its blocks skipped the norm --
+// and the launch's last report sets the loop condition to "any run still
+// iterating" (also written to any_out for the host-driven profiling path).
+// One atomic per run rather than per block: a launch over hundreds of runs
+// has hundreds of thousands of blocks.
+__device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njobs, bool reports,
+                                                    unsigned int* ticket, cudaGraphConditionalHandle cond,
+                                                    unsigned int* any_out) {
+  __shared__ bool last_run;
   __shared__ int any_go;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    last_all = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    last_run = false;
     any_go = 0;
+    if (reports) {
+      __threadfence();
+      last_run = atomicAdd(ticket, 1u) == (unsigned)njobs - 1;
+    }
   }
   __syncthreads();
-  if (!last_all) return;
+  if (!last_run) return;
   __threadfence();
   int go = 0;
   for (int q = threadIdx.x; q < njobs; q += blockDim.x) go |= __ldcg(&jobs[q].st->go);
@@ -141,10 +149,11 @@ __global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, con
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
   const NormJob& J = job_in_smem(jobs, j);
+  const int lb = blockIdx.x - start[j];
+  bool reports = lb == 0;
   if (mode == 0 || gate_open(J.st))
-    norm_mixed_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode,
-                         0);
-  batch_norm_epilogue(jobs, njobs, ticket, cond, any_out);
+    reports = norm_mixed_body<DIM>(lb, start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode, 0);
+  batch_norm_epilogue(jobs, njobs, reports, ticket, cond, any_out);
 }
 
 // The same with the double-single residual (chhs_norm_df.cuh).
@@ -156,10 +165,12 @@ __global__ void __launch_bounds__(kNdfTX * kNdfTY) kb_norm_mixed_df(const NormJo
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
   const NormJob& J = job_in_smem(jobs, j);
+  const int lb = blockIdx.x - start[j];
+  bool reports = lb == 0;
   if (mode == 0 || gate_open(J.st))
-    norm_mixed_df_body<DIM>(blockIdx.x - start[j], start[j + 1] - start[j], J.L, J.Kdf, J.G, J.partials, J.st, 0,
-                            mode, 0);
-  batch_norm_epilogue(jobs, njobs, ticket, cond, any_out);
+    reports = norm_mixed_df_body<DIM>(lb, start[j + 1] - start[j], J.L, J.Kdf, J.K, J.f64_per8, J.G, J.partials,
+                                      J.st, 0, mode, 0);
+  batch_norm_epilogue(jobs, njobs, reports, ticket, cond, any_out);
 }
 
 template <typename T>

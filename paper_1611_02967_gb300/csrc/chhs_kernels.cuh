@@ -984,7 +984,7 @@ __device__ __forceinline__ float f64_to_f32_rz(double x) {
 // right-hand side of the next inner solve: f32 = r cut to single precision,
 // e = 0, phi_b = phi cut to single precision.
 template <int DIM>
-__device__ __forceinline__ void norm_mixed_body(int bx, int nbx, const Level<double>& L, const Coefs<double>& K,
+__device__ __forceinline__ bool norm_mixed_body(int bx, int nbx, const Level<double>& L, const Coefs<double>& K,
                                                 const Level<float>& G,
                                                        double* partials, DevState* st,
                                                        cudaGraphConditionalHandle cond, int mode, int use_cond) {
@@ -1022,9 +1022,10 @@ __device__ __forceinline__ void norm_mixed_body(int bx, int nbx, const Level<dou
     last = atomicAdd(&st->ticket, 1u) == nbx - 1;
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   norm_finish(partials, nbx, L.ncell, st, cond, mode, use_cond);
+  return true;
 }
 
 template <int DIM>

@@ -70,12 +70,21 @@ __device__ __forceinline__ void ndf_block_reduce(float& sq, df64& ps, float& mx)
   __syncthreads();
 }
 
+// The double-precision pipe and the single-precision/integer pipes work at
+// the same time: a share of the blocks (f64_per8 of every 8) evaluates its
+// tile's residual with double-precision instructions (eval_N), the others in
+// double-single arithmetic; on one SM the former wait on the FP64 pipe while
+// the latter fill the issue slots.  Both write the same outputs, and the
+// residual is exact to far below the stopping tolerance either way.
+//
 // bx: the block's index among the run's nbx blocks (x-tiles fastest, then
-// y-tiles, then z-planes).
+// y-tiles, then z-planes).  Returns true in the run's last block (which took
+// the loop decision).
 template <int DIM>
-__device__ __forceinline__ void norm_mixed_df_body(int bx, int nbx, const Level<double>& L, const DfCoefs& K,
-                                                   const Level<float>& G, double* partials, DevState* st,
-                                                   cudaGraphConditionalHandle cond, int mode, int use_cond) {
+__device__ __forceinline__ bool norm_mixed_df_body(int bx, int nbx, const Level<double>& L, const DfCoefs& K,
+                                                   const Coefs<double>& K64, int f64_per8, const Level<float>& G,
+                                                   double* partials, DevState* st, cudaGraphConditionalHandle cond,
+                                                   int mode, int use_cond) {
   __shared__ df64 sP[kNdfSN], sU[kNdfSN], sQ[kNdfSN], sAx[kNdfSN], sMx[kNdfSN], sAy[kNdfSN], sMy[kNdfSN];
   __shared__ bool last;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
@@ -85,6 +94,44 @@ __device__ __forceinline__ void norm_mixed_df_body(int bx, int nbx, const Level<
   const int ty_blk = rest % gy, k = rest / gy;
   const int x0 = tx_blk * kNdfTX, y0 = ty_blk * kNdfTY;
   const int sz = nx * ny;
+  if ((bx & 7) < f64_per8) {  // this tile in double precision
+    const int tx = threadIdx.x % kNdfTX, ty = threadIdx.x / kNdfTX;
+    const int i = x0 + tx, j = y0 + ty;
+    float sq = 0.f, mx = 0.f;
+    df64 ps{0.f, 0.f};
+    if (i < nx && j < ny) {
+      const int c = i + nx * j + sz * k;
+      double n1, n2, n3;
+      eval_N<double, DIM, false>(L, K64, L.phi, L.mu, L.p, c, i, j, k, n1, n2, n3);
+      const double r1 = L.fphi[c] - n1, r2 = L.fmu[c] - n2, r3 = L.fp[c] - n3;
+      const float r1f = f64_to_f32_rz(r1), r2f = f64_to_f32_rz(r2), r3f = f64_to_f32_rz(r3);
+      const float r3s = K.s * r3f;
+      sq = r1f * r1f + r2f * r2f + r3s * r3s;
+      mx = fmaxf(fmaxf(fabsf(r1f), fabsf(r2f)), fabsf(r3s));
+      const double pc = L.p[c];
+      ps = df_split(pc);
+      G.fphi[c] = r1f;
+      G.fmu[c] = r2f;
+      G.fp[c] = r3f;
+      G.phi[c] = 0.f;
+      G.mu[c] = 0.f;
+      G.p[c] = 0.f;
+      G.phib[c] = f64_to_f32_rz(L.phi[c]);
+    }
+    ndf_block_reduce(sq, ps, mx);
+    if (threadIdx.x == 0) {
+      partials[3 * bx] = (double)sq;
+      partials[3 * bx + 1] = df_to_double(ps);
+      partials[3 * bx + 2] = (double)mx;
+      __threadfence();
+      last = atomicAdd(&st->ticket, 1u) == nbx - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    norm_finish(partials, nbx, L.ncell, st, cond, mode, use_cond);
+    return true;
+  }
   // the tile and its ring, split once
   for (int q = threadIdx.x; q < kNdfSN; q += blockDim.x) {
     const int qy = q / kNdfSW, qx = q - qy * kNdfSW;
@@ -162,19 +209,21 @@ __device__ __forceinline__ void norm_mixed_df_body(int bx, int nbx, const Level<
     last = atomicAdd(&st->ticket, 1u) == nbx - 1;
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   norm_finish(partials, nbx, L.ncell, st, cond, mode, use_cond);
+  return true;
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kNdfTX * kNdfTY) k_norm_mixed_df(const __grid_constant__ Level<double> L,
-                                                                 DfCoefs K, const __grid_constant__ Level<float> G,
+                                                                 DfCoefs K, Coefs<double> K64, int f64_per8,
+                                                                 const __grid_constant__ Level<float> G,
                                                                  double* partials, DevState* st,
                                                                  cudaGraphConditionalHandle cond, int mode,
                                                                  int use_cond) {
   pdl_enter();
-  norm_mixed_df_body<DIM>(blockIdx.x, gridDim.x, L, K, G, partials, st, cond, mode, use_cond);
+  norm_mixed_df_body<DIM>(blockIdx.x, gridDim.x, L, K, K64, f64_per8, G, partials, st, cond, mode, use_cond);
 }
 
 }  // namespace chhs_dev

@@ -324,6 +324,19 @@ def test_largest_served_sizes_satisfy_the_scheme(case, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_largest_2d_served_size_matches_oracle(precision):
+    """The largest 2D size the request loop serves (2048^2, h 0.025), one step
+    compared with the oracle's converged step element by element (the
+    property test above covers it and 256^3 at any size)."""
+    shape, h, eps, gamma, dt = (2048, 2048), 0.025, 0.05, 2.0, 0.005
+    phi0 = inputs.spinodal(shape, 21, mean=-0.1, amplitude=0.05)
+    with _run(shape, h, eps, gamma, dt, precision) as run:
+        run.set_phi(phi0)
+        run.step(1)
+        _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("gamma", [0.0, 0.5, 4.0])
 @pytest.mark.parametrize("eps", [0.02, 0.08])
 @pytest.mark.parametrize("dim", [2, 3])
