@@ -177,6 +177,39 @@ __device__ __forceinline__ void cell_ijk_small(int c, const Level<T>& L, int& i,
 //   sum M_f (mu_e - mu_c) + a_f (p_e - p_c) = Mp - sM mu_c - sa p_c, ...
 // The plain sums start from -0 (x + -0 = x exactly), so the compiler drops
 // the first addition.
+// Double to single precision with integer instructions, truncating toward
+// zero: a conversion instruction costs as much as an FP64 FMA on this GPU
+// (measured), these are a handful of integer operations.  For the values it
+// sees (residuals and phi, far inside the single-precision range) the result
+// is x with its mantissa cut to 24 bits (relative error below 2^-23);
+// magnitudes under the smallest normal single give 0 and ones beyond its
+// range give infinity.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned bits = e <= 0 ? sign : e >= 255 ? (sign | 0x7F800000u) : (sign | ((unsigned)e << 23) | mant);
+  return __uint_as_float(bits);
+}
+
+// Single to double precision with integer instructions, exactly (the
+// inverse direction of f64_to_f32_rz): exponent rebiased, mantissa moved
+// into place.  Zeros and subnormal singles give a signed zero, infinities
+// and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned mant = b & 0x7FFFFFu;
+  const unsigned hi = e == 0u ? sign
+                      : e == 255u ? (sign | 0x7FF00000u | (mant >> 3) | (mant ? 0x80000u : 0u))
+                                  : (sign | ((e + 896u) << 20) | (mant >> 3));
+  const unsigned lo = (e == 0u || e == 255u) ? 0u : (mant << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 template <typename T>
 struct Nb {
   T Mp, amu, phi, p;
@@ -348,6 +381,36 @@ __global__ void __launch_bounds__(kBlock) k_coef_restrict(Level<T> L, Coefs<T> K
 // subtraction of n_c p_c would move the smoother's fixed point).
 // The constants Ae, C, G/Dn, 1/Dn and Q (B = P'(phi), cubic_P) come from
 // coef_at; chi_a in the correction form is taken at phi_b + e.
+//
+// In the plain double-precision form the residuals R and the update of the
+// state are double precision, while the 2x2 solve that turns R into the
+// step (B, 1/(1 + Ae B) and the products with the constants) runs in single
+// precision (newton_step_f32): it only scales the step, so the sweep's fixed
+// point -- zero residual -- is the double-precision one, and the step it
+// takes differs from the exact Newton step by ~1e-7 of its length.  On
+// GB300 this removes a quarter of the cell's FP64-pipe instructions.
+struct StepF32 {
+  float dphi, dmu, dp;
+};
+
+// The 2x2 Newton solve in single precision from the double-precision
+// residuals R1, R2, R3 (R3 not yet scaled by 1/Dn) and B's terms t, t2 at
+// the cell's phi (cell_update); the Jacobian constants are cut to single
+// precision with integer instructions.
+__device__ __forceinline__ StepF32 newton_step_f32(double R1, double R2, double R3, double phic, double t,
+                                                   double t2, double Ae, double cC, double cGn, double cHn) {
+  const float v = f64_to_f32_rz(phic), tf = f64_to_f32_rz(t), t2f = f64_to_f32_rz(t2);
+  const float B = (0.25f * v + tf) * v + t2f;
+  const float ae = f64_to_f32_rz(Ae);
+  const float r2 = f64_to_f32_rz(R2);
+  const float r3n = f64_to_f32_rz(cHn) * f64_to_f32_rz(R3);
+  StepF32 d;
+  d.dphi = ((f64_to_f32_rz(R1) - ae * r2) - f64_to_f32_rz(cC) * r3n) * rcp_approx(1.f + ae * B);
+  d.dmu = r2 + B * d.dphi;
+  d.dp = r3n - f64_to_f32_rz(cGn) * d.dmu;
+  return d;
+}
+
 template <typename T, int DIM, bool CORR>
 __device__ __forceinline__ void cell_update(const Level<T>& L, const Coefs<T>& K, int c, int i, int j,
                                             int k, T f1, T f2, T f3) {
@@ -357,26 +420,34 @@ __device__ __forceinline__ void cell_update(const Level<T>& L, const Coefs<T>& K
   T sM = L.sM[c], sa = L.sa[c], Q = L.cQ[c];
   T hp = L.cH[c];
   T R1 = (f1 - phic) + L.sih2 * ((S.Mp - sM * muc) - sa * pc);
-  T R2, B;
+  T R2, B, t = T(0), t2 = T(0);
   if (CORR) {
     R2 = f2 - muc + chi_term<T, CORR>(L, c, phic, L.phim[c]) - L.e34ih2 * (S.phi - count_value<T>(S.m) * phic);
     const T w = L.phib[c] + phic;
     B = (T(0.75) * w + (hp + hp)) * w + Q;
   } else {
     // cubic_P(v) = t2 v with t = v/4 + pm/4, t2 = t v + Q; P'(v) = (t + v/4) v + t2
-    const T t = T(0.25) * phic + hp;
-    const T t2 = t * phic + Q;
+    t = T(0.25) * phic + hp;
+    t2 = t * phic + Q;
     R2 = ((f2 - muc) - L.e34ih2 * S.phi) + t2 * phic;
     B = (T(0.25) * phic + t) * phic + t2;
   }
-  T R3n = L.cHn[c] * (f3 + L.ih2 * ((S.p - count_value<T>(S.m) * pc) + K.gamma * (S.amu - sa * muc)));
-  T Ae = L.cAe[c];
-  T dphi = ((R1 - Ae * R2) - L.cC[c] * R3n) * rcp_approx(T(1) + Ae * B);
-  T dmu = R2 + B * dphi;
-  T dp = R3n - L.cGn[c] * dmu;
-  L.phi[c] = phic + dphi;
-  L.mu[c] = muc + dmu;
-  L.p[c] = pc + dp;
+  const T R3 = f3 + L.ih2 * ((S.p - count_value<T>(S.m) * pc) + K.gamma * (S.amu - sa * muc));
+  if constexpr (sizeof(T) == 8 && !CORR) {
+    const StepF32 d = newton_step_f32(R1, R2, R3, phic, t, t2, L.cAe[c], L.cC[c], L.cGn[c], L.cHn[c]);
+    L.phi[c] = phic + f32_to_f64_exact(d.dphi);
+    L.mu[c] = muc + f32_to_f64_exact(d.dmu);
+    L.p[c] = pc + f32_to_f64_exact(d.dp);
+  } else {
+    T R3n = L.cHn[c] * R3;
+    T Ae = L.cAe[c];
+    T dphi = ((R1 - Ae * R2) - L.cC[c] * R3n) * rcp_approx(T(1) + Ae * B);
+    T dmu = R2 + B * dphi;
+    T dp = R3n - L.cGn[c] * dmu;
+    L.phi[c] = phic + dphi;
+    L.mu[c] = muc + dmu;
+    L.p[c] = pc + dp;
+  }
 }
 
 // The right-hand side at cell c for a smoothing pass.  With rhs set (the
@@ -455,10 +526,12 @@ __device__ __forceinline__ void for_faces(const Level<double>& L, int c, int i, 
 
 // x: this lane's four exchange slots, stride 32.  bar() synchronises the
 // three warps of the group; every warp of the group calls this the same
-// number of times (act may be false).
+// number of times (act may be false).  As in cell_update, the residual rows
+// are double precision and the 2x2 solve is single precision: warp 1 hands
+// over R3/Dn, warp 2 R2, B and 1/(1 + Ae B), all in single precision.
 template <int DIM, class BAR>
 __device__ __forceinline__ void cell_update_split(const Level<double>& L, const Coefs<double>& K, int role,
-                                                  bool act, int c, int i, int j, int k, bool rhs, double* x,
+                                                  bool act, int c, int i, int j, int k, bool rhs, float* x,
                                                   BAR bar) {
   const double* af[3] = {L.ax, L.ay, L.az};
   const double* Mf[3] = {L.Mx, L.My, L.Mz};
@@ -516,7 +589,8 @@ __device__ __forceinline__ void cell_update_split(const Level<double>& L, const 
         f3 += -L.ih2 * ((sp0 - mm * L.p0[c]) + K.gamma * (amu0 - sa * L.mu0[c]));
         L.fp[c] = f3;
       }
-      x[0] = L.cHn[c] * (f3 + L.ih2 * ((sp - mm * L.p[c]) + K.gamma * (amu - sa * L.mu[c])));
+      const double R3 = f3 + L.ih2 * ((sp - mm * L.p[c]) + K.gamma * (amu - sa * L.mu[c]));
+      x[0] = f64_to_f32_rz(L.cHn[c]) * f64_to_f32_rz(R3);
     } else {
       double sphi = -0.0;
       for_faces<DIM>(L, c, i, j, k, [&](bool in, int es, int fs, int d) {
@@ -537,21 +611,23 @@ __device__ __forceinline__ void cell_update_split(const Level<double>& L, const 
       const double t = 0.25 * v + hp;
       const double t2 = t * v + Q;
       const double R2 = ((f2 - L.mu[c]) - L.e34ih2 * sphi) + t2 * v;
-      const double B = (0.25 * v + t) * v + t2;
-      x[32] = R2;
+      const float vf = f64_to_f32_rz(v);
+      const float B = (0.25f * vf + f64_to_f32_rz(t)) * vf + f64_to_f32_rz(t2);
+      x[32] = f64_to_f32_rz(R2);
       x[64] = B;
-      x[96] = rcp_approx(1.0 + L.cAe[c] * B);
+      x[96] = rcp_approx(1.f + f64_to_f32_rz(L.cAe[c]) * B);
     }
   }
   bar();
   if (act && role == 0) {
-    const double R3n = x[0], R2 = x[32], B = x[64], rd = x[96];
-    const double dphi = ((R1 - Ae * R2) - cC * R3n) * rd;
-    const double dmu = R2 + B * dphi;
-    const double dp = R3n - cGn * dmu;
-    L.phi[c] = phic + dphi;
-    L.mu[c] = muc + dmu;
-    L.p[c] = pc + dp;
+    const float R3n = x[0], R2 = x[32], B = x[64], rd = x[96];
+    const float ae = f64_to_f32_rz(Ae);
+    const float dphi = ((f64_to_f32_rz(R1) - ae * R2) - f64_to_f32_rz(cC) * R3n) * rd;
+    const float dmu = R2 + B * dphi;
+    const float dp = R3n - f64_to_f32_rz(cGn) * dmu;
+    L.phi[c] = phic + f32_to_f64_exact(dphi);
+    L.mu[c] = muc + f32_to_f64_exact(dmu);
+    L.p[c] = pc + f32_to_f64_exact(dp);
   }
 }
 
@@ -560,7 +636,7 @@ __device__ __forceinline__ void cell_update_split(const Level<double>& L, const 
 template <int DIM>
 __global__ void __launch_bounds__(96) k_smooth_split(Level<double> L, Coefs<double> K, int colour, int rhs) {
   pdl_enter();
-  __shared__ double xch[4 * 32];
+  __shared__ float xch[4 * 32];
   const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int hw = (L.nx + 1) >> 1;
   const int t = blockIdx.x * 32 + lane;
@@ -963,23 +1039,6 @@ __global__ void __launch_bounds__(kBlock) k_coef_restrict_f32(Level<double> F, L
   coef_restrict_f32_body<DIM>(blockIdx.x, F, G, K, Gn, has_next);
 }
 
-// Double to single precision with integer instructions, truncating toward
-// zero: a conversion instruction costs as much as an FP64 FMA on this GPU
-// (measured), these are a handful of integer operations.  For the values it
-// sees (residuals and phi, far inside the single-precision range) the result
-// is x with its mantissa cut to 24 bits (relative error below 2^-23);
-// magnitudes under the smallest normal single give 0 and ones beyond its
-// range give infinity.
-__device__ __forceinline__ float f64_to_f32_rz(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  const unsigned bits = e <= 0 ? sign : e >= 255 ? (sign | 0x7F800000u) : (sign | ((unsigned)e << 23) | mant);
-  return __uint_as_float(bits);
-}
-
 // The stopping norm of the double-precision iterate, as k_norm, and the
 // right-hand side of the next inner solve: f32 = r cut to single precision,
 // e = 0, phi_b = phi cut to single precision.
@@ -1145,7 +1204,7 @@ __device__ __forceinline__ void tail_smooth(const Level<T>& L, const Coefs<T>& K
   if constexpr (!CORR && sizeof(T) == 8) {
     // plain double precision: split update, groups of three warps, named
     // barrier per group; every group runs the same number of rounds
-    __shared__ double xch[2][kTailGroups][4 * 32];
+    __shared__ float xch[2][kTailGroups][4 * 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = warp / 3, role = warp - 3 * g;
     if (g < kTailGroups) {
