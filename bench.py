@@ -380,56 +380,18 @@ SERVED_DESC = ("served sample of the serving configuration: 60 runs, half 2D (n 
                "active slots, 5 steps per slice")
 
 
-def served_leg(capacity_cell_steps_per_s, seed=5, nruns=60):
-    """Continuous batching through chhs_server_*: returns latency percentiles
-    and throughput of a seeded Poisson stream of runs drawn from the serving
-    configuration's size and parameter ranges."""
-    import numpy as np
-
-    from paper_1611_02967_gb300 import chhs, inputs
-    u = inputs.uniform01(seed, nruns * 7, stream=11).reshape(nruns, 7)
-    three_d = u[:, 5] < 0.5
-    n2 = np.array([128, 256, 512, 1024, 2048])[np.minimum((u[:, 0] * 5).astype(int), 4)]
-    n3 = np.array([64, 128, 256])[np.minimum((u[:, 0] * 3).astype(int), 2)]
-    sizes = np.where(three_d, n3, n2)
-    steps = 10 + (u[:, 1] * 41).astype(int)
-    eps = 0.02 + 0.06 * u[:, 2]
-    gamma = 0.5 + 3.5 * u[:, 3]
-    cells = np.where(three_d, sizes.astype(float) ** 3, sizes.astype(float) ** 2)
-    work = cells * steps
-    rate = 0.8 * capacity_cell_steps_per_s / work.mean()        # runs per second
-    gaps = -np.log(1.0 - u[:, 4]) / rate                         # exponential inter-arrival times
-    shapes, hs, phis = [], [], []
-    for k in range(nruns):
-        n = int(sizes[k])
-        if three_d[k]:
-            shapes.append((n, n, n))
-            hs.append(0.05)
-            phis.append(inputs.bubbles(n, n * 0.05, eps[k], seed * 1000 + k, count=4) if n <= 128
-                        else inputs.spinodal((n, n, n), seed * 1000 + k, mean=0.0))
-        else:
-            shapes.append((n, n))
-            hs.append(0.025)
-            phis.append(inputs.spinodal((n, n), seed * 1000 + k, mean=0.0))
-    with chhs.Server(pool_bytes=48 << 30, max_active=12, steps_per_slice=5) as sv:
-        t0 = time.perf_counter()
-        t_next = t0
-        ids = []
-        for k in range(nruns):
-            t_next += gaps[k]
-            while time.perf_counter() < t_next:
-                time.sleep(0.0002)
-            ids.append(sv.submit(shapes[k], hs[k], eps[k], gamma[k], 0.005, int(steps[k]), phis[k], precision=1))
-        for rid in ids:
-            sv.wait(rid, 600.0)
-        res = [sv.result(rid, with_phi=False) for rid in ids]
-    ok = all(r["status"] == 0 for r in res)
-    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
-    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "value": float(work.sum() / span), "unit": UNIT,
-            "offered_load": 0.8, "runs": nruns, "all_converged": ok,
-            "vcycles_per_step": float(sum(r["vcycles"] for r in res) / steps.sum()), "sample": SERVED_DESC}
+def served_leg(capacity_cell_steps_per_s, nruns=60):
+    """Continuous batching through chhs_server_*: latency percentiles and
+    throughput of a seeded Poisson stream of runs drawn from the serving
+    configuration's size and parameter ranges (experiments.serving_runs),
+    with the step range shortened to 10-50 so that the leg ends in about
+    half a minute."""
+    from paper_1611_02967_gb300 import experiments as ex
+    runs, u_gap = ex.serving_runs(nruns, steps=(10, 50))
+    res, span = ex.serve(runs, ex.serve_arrivals(runs, u_gap, 0.8 * capacity_cell_steps_per_s))
+    out = ex.serving_summary(runs, res, span, 0.8)
+    out.update(unit=UNIT, sample=SERVED_DESC)
+    return out
 
 
 def e2e_steps(run, state, steps, ncell):
@@ -593,7 +555,8 @@ def run_ours(args):
     max_ms = reduce_max(dev_ms, world)
     units = reduce_sum(float(ncell * args.steps), world)
     value = units / (max_ms / 1e3)
-    launches = args.steps * (per_step + 1) + vtot * per_v
+    checks = run.norm_checks()  # stopping norms after V-cycles: one kernel each
+    launches = 1 + args.steps * per_step + vtot * per_v + checks
 
     # end to end through the public API with host-resident state: every step
     # copies (phi^m, phi^{m-1}, mu, p) in from pinned host memory, solves, and
@@ -693,7 +656,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config(world), "vcycles_per_step": vtot / args.steps, "final_resid": resid,
+                "config": config(world), "vcycles_per_step": vtot / args.steps, "norms_per_step": checks / args.steps, "final_resid": resid,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "mixed": mixed, "served": served, "batched": batched, "bubbles128": bubbles,
                 "tuning": tuning,
                 "cpu_baseline": cpu,

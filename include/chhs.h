@@ -74,6 +74,14 @@ typedef struct {
                           single-precision pipes, which run 64 times faster on GB300.  Either
                           way the stopping norm is that of the double-precision iterate.  Not 0
                           or 1: CHHS_ERR_INVALID_ARG. */
+    int max_inner;     /* most V-cycles between two stopping norms, 1..3 (default 3; otherwise
+                          CHHS_ERR_INVALID_ARG).  After each norm the device predicts, from the
+                          contraction per V-cycle it has measured, how many V-cycles the norm
+                          still needs to reach tol (rounded down, at least 1, at most max_inner)
+                          and runs that many before the next norm; in the mixed form they are
+                          the correction V-cycles of one defect-correction iteration.  A step
+                          still ends only on a norm at or below tol.  1: a norm after every
+                          V-cycle. */
 } chhs_opts;
 
 /* Fill *opts with the defaults above.  Returns CHHS_ERR_INVALID_ARG on NULL. */
@@ -140,8 +148,16 @@ chhs_status chhs_wait(chhs_t* run, int* vcycles_out, double* resid_out);
 /* Kernel launches of one time step's graph: *per_vcycle for each V-cycle and
  * *per_step for the frame around the V-cycle loop (setup, restrictions of
  * phi^m and phi*, the initial norm, the mean of p and the accepted step).
- * A step with V cycles launches per_step + V * per_vcycle kernels. */
+ * A step with V cycles and C stopping norms after them (chhs_norm_checks)
+ * launches per_step + V * per_vcycle + C kernels (one per norm). */
 chhs_status chhs_launch_counts(const chhs_t* run, int* per_vcycle, int* per_step);
+
+/* Stopping norms evaluated after V-cycles during the steps of the last
+ * completed chhs_step (or chhs_step_async and chhs_wait), summed over them:
+ * with max_inner > 1 fewer than the V-cycles.  Read from the handle's host
+ * copy of the device state; no device work.  NULL argument:
+ * CHHS_ERR_INVALID_ARG. */
+chhs_status chhs_norm_checks(const chhs_t* run, int* checks);
 
 /* Kernel kinds reported by chhs_profile_step. */
 enum {
@@ -430,14 +446,18 @@ chhs_t* chhs_batch_run(chhs_batch_t* batch, int r);
 chhs_status chhs_batch_step(chhs_batch_t* batch, int nsteps, int* status_out, int* vcycles_out, double* resid_out);
 
 /* Launches of the batch's step graph: per V-cycle and per step outside the
- * V-cycle loop, whatever the number of runs. */
+ * V-cycle loop, whatever the number of runs (plus one batched norm launch
+ * per iteration of the loop).  With opts.max_inner > 1 each run takes the
+ * V-cycles between norms that its own norms predict, as it would alone: the
+ * graph runs a 2nd (3rd) batched V-cycle in an iteration when some run asks
+ * for one, gated off for the others. */
 chhs_status chhs_batch_launch_counts(const chhs_batch_t* batch, int* per_vcycle, int* per_step);
 
 /* One time step of every run launched kernel by kernel (no graph) with a
  * CUDA event pair around each batched launch; adds into the caller's arrays
  * of CHHS_K_COUNT entries the device milliseconds and launches per kernel
  * kind (as chhs_profile_step).  For profiling: the host reads the "any run
- * iterating" flag after every V-cycle.  Errors: CHHS_ERR_INVALID_ARG (NULL
+ * iterating" flags after every norm.  Errors: CHHS_ERR_INVALID_ARG (NULL
  * argument), CHHS_ERR_CUDA. */
 chhs_status chhs_batch_profile_step(chhs_batch_t* batch, double* ms_out, long long* launches_out);
 

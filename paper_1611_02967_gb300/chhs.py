@@ -30,7 +30,8 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity",
            "chhs_autotune", "chhs_batch_workspace_bytes", "chhs_batch_create", "chhs_batch_size", "chhs_batch_run",
            "chhs_batch_step", "chhs_batch_launch_counts", "chhs_batch_last_error", "chhs_batch_destroy",
-           "chhs_profile_smooth32", "chhs_probe_fp64", "chhs_batch_profile_step", "chhs_set_tuning"]
+           "chhs_profile_smooth32", "chhs_probe_fp64", "chhs_batch_profile_step", "chhs_set_tuning",
+           "chhs_norm_checks"]
 
 # kernel kinds of chhs_profile_step
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
@@ -39,7 +40,8 @@ K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm
 class chhs_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_v", ctypes.c_int),
                 ("coarsest", ctypes.c_int), ("tol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("max_factor", ctypes.c_double), ("coarsest_f64", ctypes.c_int), ("f64_residual", ctypes.c_int)]
+                ("max_factor", ctypes.c_double), ("coarsest_f64", ctypes.c_int), ("f64_residual", ctypes.c_int),
+                ("max_inner", ctypes.c_int)]
 
 
 class chhs_request(ctypes.Structure):
@@ -89,6 +91,7 @@ def lib():
             "chhs_step_async": (i, [_vp, i]),
             "chhs_wait": (i, [_vp, _ip, _dp]),
             "chhs_launch_counts": (i, [_vp, _ip, _ip]),
+            "chhs_norm_checks": (i, [_vp, _ip]),
             "chhs_profile_step": (i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
             "chhs_mass": (i, [_vp, _dp]),
             "chhs_energy": (i, [_vp, _dp, _dp]),
@@ -278,6 +281,12 @@ class Run:
         b = ctypes.c_int(0)
         self._check(lib().chhs_launch_counts(self.handle, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def norm_checks(self):
+        """Stopping norms after V-cycles in the last completed step call."""
+        c = ctypes.c_int(0)
+        self._check(lib().chhs_norm_checks(self.handle, ctypes.byref(c)))
+        return c.value
 
     def profile_step(self, acc=None):
         """One step launched kernel by kernel with events; accumulates into

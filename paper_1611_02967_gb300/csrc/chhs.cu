@@ -134,7 +134,8 @@ Layout make_layout(int dim, const int n[3], int coarsest, int precision) {
 bool valid_opts(const chhs_opts& o) {
   return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.max_v >= 1 && o.coarsest >= 2 &&
          o.tol > 0 && (o.precision == 0 || o.precision == 1) && o.max_factor >= 0 &&
-         (o.coarsest_f64 == 0 || o.coarsest_f64 == 1) && (o.f64_residual == 0 || o.f64_residual == 1);
+         (o.coarsest_f64 == 0 || o.coarsest_f64 == 1) && (o.f64_residual == 0 || o.f64_residual == 1) &&
+         o.max_inner >= 1 && o.max_inner <= kMaxInner;
 }
 
 bool valid_problem(int dim, const int n[3], double h, double eps, double gamma, double dt) {
@@ -202,6 +203,7 @@ struct chhs {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches_per_v = 0, launches_per_step = 0;
+  bool vc_update = true;  // while enqueueing: this V-cycle ends with the update u <- u + e (mixed form)
   bool pending = false;  // steps enqueued by chhs_step_async since the last chhs_wait
   int* counter = nullptr;  // counts launches while the graph is captured
   Prof* prof = nullptr;  // per-launch events while profiling
@@ -364,19 +366,19 @@ struct Enqueue {
         Lb.fp = L.fc3;
       }
       TileOut<T> to_state{L.phi, L.mu, L.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-      if (l == 0 && fused_update(run)) {  // the finished correction goes straight into u
+      if (l == 0 && fused_update(run) && run->vc_update) {  // the finished correction goes straight into u
         to_state.phi64 = run->lev[0].phi;
         to_state.mu64 = run->lev[0].mu;
         to_state.p64 = run->lev[0].p;
       }
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_pre(run, l), [&] {
         pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T), tw, th), s, L, C,
-                 K, np1, np1 + 1, rhs ? 1 : 0, 0, 1, to_copy, (const DevState*)nullptr, tw, th);
+                 K, np1, np1 + 1, rhs ? 1 : 0, 0, 1, to_copy, (const int*)nullptr, tw, th);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_post(run, l), [&] {
         pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T), tw, th), s, Lb, C, K,
-                 np2, np2, 0, 1, 0, to_state, (const DevState*)nullptr, tw, th);
+                 np2, np2, 0, 1, 0, to_state, (const int*)nullptr, tw, th);
       });
       return;
     }
@@ -447,7 +449,7 @@ struct Enqueue {
     for (int it = 0; it < nu2; ++it)
       for (int colour = 0; colour < 2; ++colour) {
         const int pro = it == 0 ? (colour == 0 ? 1 : 2) : 0;
-        const bool upd = l == 0 && fused_update(run) && it == nu2 - 1 && colour == 1;
+        const bool upd = l == 0 && fused_update(run) && run->vc_update && it == nu2 - 1 && colour == 1;
         launch(run, s, kind, colour_cells(L, colour), [&] {
           pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, 0, pro, upd ? run->lev[0] : none);
         });
@@ -535,20 +537,25 @@ struct Enqueue {
     });
   }
 
-  // One iteration of the step's loop: a double-precision V-cycle, or a
-  // single-precision correction V-cycle and the double-precision update.
-  static void iteration(chhs_t* run, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+  // One V-cycle of the step's loop: a double-precision V-cycle, or a
+  // single-precision correction V-cycle, followed (update) by the
+  // double-precision update u <- u + e.  An iteration of the loop runs
+  // DevState::inner V-cycles, the update after the last only (the ones before
+  // continue the same correction equation from the correction they leave),
+  // then the stopping norm.
+  static void vcycle_step(chhs_t* run, cudaStream_t s, bool update) {
     if (mixed(run)) {
+      run->vc_update = update;
       vcycle<float, true>(run, s, run->lev32, run->tail32, 0);
+      run->vc_update = true;
       const Level<double>& L = run->lev[0];
-      if (!fused_update(run))
+      if (update && !fused_update(run))
         launch(run, s, CHHS_K_FRAME, 1.0, [&] {
           pdl(k_mixed_update, nblocks(L.ncell), kBlock, s, L, run->lev32[0]);
         });
     } else {
       vcycle<double, false>(run, s, run->lev, run->tail, 0);
     }
-    norm(run, s, cond, 1, use_cond);
   }
 
   // The step's set-up: phi*, f, the initial guess and the finest level's
@@ -609,10 +616,10 @@ struct Enqueue {
     // capture streams and fork/join events, released on every return path (a
     // capture that an error interrupted is ended and its graph dropped first)
     struct CaptureRes {
-      cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+      cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};
       cudaEvent_t e[2] = {nullptr, nullptr};
       ~CaptureRes() {
-        for (int q : {1, 0}) {
+        for (int q : {3, 1, 0}) {
           cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
           if (s[q] && cudaStreamIsCapturing(s[q], &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
             cudaGraph_t g = nullptr;
@@ -630,11 +637,12 @@ struct Enqueue {
     CU(cudaStreamCreateWithFlags(&res.s[0], cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&res.s[1], cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&res.s[2], cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&res.s[3], cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&res.e[0], cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&res.e[1], cudaEventDisableTiming));
-    cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2];
+    cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2], cs4 = res.s[3];
     cudaEvent_t fork = res.e[0], join = res.e[1];
-    int n_frame = 0, n_v = 0;
+    int n_frame = 0, n_v = 0, n_other = 0;
     CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     run->counter = &n_frame;
     frame_setup(run, cs);
@@ -663,8 +671,33 @@ struct Enqueue {
     CU(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    // the loop body: IF (inner >= 3) V-cycle; IF (inner >= 2) V-cycle; the
+    // V-cycle with the update; the stopping norm, which sets the loop
+    // condition and the two IF conditions for the next iteration
+    const int n_if = std::min(run->opts.max_inner, kMaxInner) - 1;
+    cudaGraphConditionalHandle cif[2] = {0, 0};
+    for (int q = n_if - 1; q >= 0; --q) {
+      cudaGraph_t bg = nullptr;
+      CU(cudaStreamGetCaptureInfo(cs2, &cst, nullptr, &bg, &deps, nullptr, &ndeps));
+      CU(cudaGraphConditionalHandleCreate(&cif[q], bg, 0, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams ip{};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = cif[q];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t ifn;
+      CU(cudaGraphAddNode(&ifn, bg, deps, nullptr, ndeps, &ip));
+      CU(cudaStreamUpdateCaptureDependencies(cs2, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t ib = ip.conditional.phGraph_out[0];
+      CU(cudaStreamBeginCaptureToGraph(cs4, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      run->counter = &n_other;
+      vcycle_step(run, cs4, false);
+      CU(cudaStreamEndCapture(cs4, &ib));
+    }
     run->counter = &n_v;
-    iteration(run, cs2, cond, 1);
+    vcycle_step(run, cs2, true);
+    run->counter = &n_other;
+    norm(run, cs2, cond, 1, 1);
     CU(cudaStreamEndCapture(cs2, &body));
     run->counter = &n_frame;
     frame_tail(run, cs);
@@ -673,6 +706,14 @@ struct Enqueue {
     CU(cudaGraphInstantiate(&run->exec, run->graph, 0));
     run->launches_per_v = n_v;
     run->launches_per_step = n_frame;
+    // the IF nodes' handles, for the norm kernels that set them
+    struct {
+      int use_if;
+      cudaGraphConditionalHandle h[2];
+    } ifs{std::max(n_if, 0), {cif[0], cif[1]}};
+    CU(cudaMemcpyAsync(&run->st->use_if, &ifs.use_if, sizeof(int), cudaMemcpyHostToDevice, run->stream));
+    CU(cudaMemcpyAsync(run->st->cond_if, ifs.h, sizeof(ifs.h), cudaMemcpyHostToDevice, run->stream));
+    CU(cudaStreamSynchronize(run->stream));
     return CHHS_OK;
   }
 
@@ -685,7 +726,9 @@ struct Enqueue {
       CU(cudaMemcpyAsync(run->host_st, run->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       if (!run->host_st->go) break;
-      iteration(run, s, 0, 0);
+      const int inner = std::max(1, run->host_st->inner);
+      for (int q = 0; q < inner; ++q) vcycle_step(run, s, q == inner - 1);
+      norm(run, s, 0, 1, 0);
     }
     frame_tail(run, s);
     CU(cudaGetLastError());
@@ -724,13 +767,15 @@ struct Enqueue {
   }
 };
 
-__global__ void k_reset_call(DevState* st, double tol, double tol_max, int max_v) {
+__global__ void k_reset_call(DevState* st, double tol, double tol_max, int max_v, int max_inner) {
   st->failed = 0;
   st->vtotal = 0;
   st->steps_done = 0;
+  st->checks = 0;
   st->tol = tol;
   st->tol_max = tol_max;
   st->max_v = max_v;
+  st->max_inner = max_inner;
 }
 
 // The pointwise guard's bound (infinite when the guard is off).
@@ -914,6 +959,7 @@ chhs_status chhs_default_opts(chhs_opts* o) {
   o->max_factor = 50.0;
   o->coarsest_f64 = 0;
   o->f64_residual = 0;
+  o->max_inner = kMaxInner;
   return CHHS_OK;
 }
 
@@ -974,7 +1020,8 @@ chhs_status chhs_step_async(chhs_t* run, int nsteps) {
   if (nsteps < 0) return fail(run, CHHS_ERR_INVALID_ARG, "nsteps < 0");
   run->err.clear();
   if (!run->pending) {  // the first call since the last wait starts a new count
-    k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, tol_max_of(run->opts), run->opts.max_v);
+    k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, tol_max_of(run->opts), run->opts.max_v,
+                                           run->opts.max_inner);
     CU(cudaGetLastError());
     run->pending = true;
   }
@@ -1017,6 +1064,12 @@ chhs_status chhs_launch_counts(const chhs_t* run, int* per_vcycle, int* per_step
   return CHHS_OK;
 }
 
+chhs_status chhs_norm_checks(const chhs_t* run, int* checks) {
+  if (!run || !checks) return CHHS_ERR_INVALID_ARG;
+  *checks = run->host_st ? run->host_st->checks : 0;
+  return CHHS_OK;
+}
+
 chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_out, double* units_out) {
   if (!run || !ms_out || !launches_out || !units_out) return fail(run, CHHS_ERR_INVALID_ARG, "NULL argument");
   // it resets the step counters, which would drop a pending step's status
@@ -1024,7 +1077,8 @@ chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_o
   run->err.clear();
   Prof prof;
   run->prof = &prof;
-  k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, tol_max_of(run->opts), run->opts.max_v);
+  k_reset_call<<<1, 1, 0, run->stream>>>(run->st, run->opts.tol, tol_max_of(run->opts), run->opts.max_v,
+                                         run->opts.max_inner);
   chhs_status s = run->dim == 2 ? Enqueue<2>::profile_step(run) : Enqueue<3>::profile_step(run);
   run->prof = nullptr;
   if (s != CHHS_OK) return s;
@@ -1120,7 +1174,7 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
       pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
     else
       pdl_grid(k_tile<float, true>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4, tw, th),
-               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy, (const DevState*)nullptr, tw, th);
+               run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy, (const int*)nullptr, tw, th);
   }
   CU(cudaGetLastError());
   CU(cudaEventRecord(ev.b, run->stream));
@@ -1464,6 +1518,7 @@ struct chhs_batch {
   bool own_stream = false;
   DevState** d_sts = nullptr;       // per run, for the reset and gather kernels
   unsigned int* d_ticket = nullptr; // blocks of a batched norm launch that have finished
+  BatchConds* d_conds = nullptr;    // the step graph's loop and IF conditions
   int* d_out = nullptr;             // status[n], vcycles[n], then resid[n] (doubles)
   char* h_out = nullptr;            // pinned mirror of d_out
   cudaGraph_t graph = nullptr;
@@ -1506,6 +1561,13 @@ template <int DIM>
 struct BatchStep {
   chhs_batch_t* b;
   bool capture = false;
+  // the V-cycle being emitted: 1 ends an iteration (gate go, with the
+  // update u <- u + e), 2 and 3 are the extra V-cycles before it (gates go2,
+  // go3, no update) that a run takes when its norm predicted them
+  int vk = 1;
+  const int* gate(const chhs_t* r) const { return vk == 1 ? &r->st->go : vk == 2 ? &r->st->go2 : &r->st->go3; }
+  int n_if() const { return std::min(b->opts.max_inner, kMaxInner) - 1; }
+  size_t vstart[kMaxInner + 1] = {};  // table positions of the V-cycles vk = 1..3 and the norm after them (plan)
   std::vector<char> buf;            // host image of the job tables
   std::vector<size_t> offs;         // table offsets in emission order
   size_t cur = 0;
@@ -1604,7 +1666,8 @@ struct BatchStep {
     }
   }
 
-  void norm(cudaStream_t s, cudaGraphConditionalHandle cond, int mode) {
+  void norm(cudaStream_t s, bool use_cond, int mode) {
+    const BatchConds* cc = use_cond ? b->d_conds : nullptr;
     JobList<NormJob> jl;
     const bool df = !b->opts.f64_residual;
     for (chhs_t* r : b->runs) {
@@ -1613,9 +1676,9 @@ struct BatchStep {
              df ? (int)ndf_blocks(L.nx, L.ny, L.nz) : r->norm_blocks);
     }
     if (df)
-      go(CHHS_K_NORM, jl, kb_norm_mixed_df<DIM>, kNdfTX * kNdfTY, 0, s, b->d_ticket, cond, mode, b->d_ticket + 1);
+      go(CHHS_K_NORM, jl, kb_norm_mixed_df<DIM>, kNdfTX * kNdfTY, 0, s, b->d_ticket, cc, mode, b->d_ticket + 1);
     else
-      go(CHHS_K_NORM, jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cond, mode, b->d_ticket + 1);
+      go(CHHS_K_NORM, jl, kb_norm_mixed<DIM>, kBlock, 0, s, b->d_ticket, cc, mode, b->d_ticket + 1);
   }
 
   void vcycle(cudaStream_t s) {
@@ -1623,13 +1686,14 @@ struct BatchStep {
     const int nu1 = b->opts.nu1, nu2 = b->opts.nu2;
     for (int l = 0; l < ts; ++l) pre(s, l, nu1);
     std::vector<TailJob<float>> tails;
-    for (chhs_t* r : b->runs) tails.push_back(TailJob<float>{r->tail32, k32(r), r->st});
+    for (chhs_t* r : b->runs) tails.push_back(TailJob<float>{r->tail32, k32(r), gate(r)});
     go_tail(tails, s);
     for (int l = ts - 1; l >= 0; --l) post(s, l, nu2);
+    if (vk != 1) return;
     JobList<PairJob> upd;
     for (chhs_t* r : b->runs)
       if (!Enqueue<DIM>::fused_update(r))
-        upd.add(PairJob{r->lev32[0], r->lev32[0], k32(r), r->lev[0], r->st}, nblocks(r->lev[0].ncell));
+        upd.add(PairJob{r->lev32[0], r->lev32[0], k32(r), r->lev[0], gate(r)}, nblocks(r->lev[0].ncell));
     go(CHHS_K_FRAME, upd, kb_mixed_update, kBlock, 0, s);
   }
 
@@ -1690,7 +1754,7 @@ struct BatchStep {
         const Level<float>& L = r->lev32[l];
         const TileOut<float> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3, nullptr, nullptr, nullptr};
         const int gx = (L.nx + kTileW - 1) / kTileW, gy = (L.ny + kTileH - 1) / kTileH;
-        jl.add(TileJob<float>{L, r->lev32[l + 1], k32(r), to_copy, r->st, np1, np1 + 1, l > 0 ? 1 : 0, 0, 1, gx},
+        jl.add(TileJob<float>{L, r->lev32[l + 1], k32(r), to_copy, gate(r), np1, np1 + 1, l > 0 ? 1 : 0, 0, 1, gx},
                gx * gy);
       }
       tiles(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, s);
@@ -1703,7 +1767,7 @@ struct BatchStep {
     if (l > 0 && nu1 == 0) {
       JobList<PairJob> jl;
       runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
-        jl.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, nblocks(L.ncell));
+        jl.add(PairJob{L, C, k32(r), Level<double>{}, gate(r)}, nblocks(L.ncell));
       });
       go(CHHS_K_COARSE_RHS, jl, kb_coarse_rhs<DIM>, kBlock, 0, s);
     }
@@ -1712,7 +1776,7 @@ struct BatchStep {
         JobList<SmoothCJob> jl;
         runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
           const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
-          jl.add(SmoothCJob{L, C, Level<double>{}, k32(r), r->st, colour, (l > 0 && it == 0) ? 1 : 0, 0},
+          jl.add(SmoothCJob{L, C, Level<double>{}, k32(r), gate(r), colour, (l > 0 && it == 0) ? 1 : 0, 0},
                  (threads + kSmoothBlock - 1) / kSmoothBlock);
         });
         go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
@@ -1721,7 +1785,7 @@ struct BatchStep {
     runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
       constexpr int TX = DIM == 3 ? 8 : 16;
       const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
-      jr.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, (int)((tiles * 32 + kBlock - 1) / kBlock));
+      jr.add(PairJob{L, C, k32(r), Level<double>{}, gate(r)}, (int)((tiles * 32 + kBlock - 1) / kBlock));
     });
     go(CHHS_K_RESTRICT, jr, kb_residual_restrict_c<DIM>, kBlock, 0, s);
   }
@@ -1743,13 +1807,13 @@ struct BatchStep {
           Lb.fp = L.fc3;
         }
         TileOut<float> to_state{L.phi, L.mu, L.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-        if (l == 0 && Enqueue<DIM>::fused_update(r)) {
+        if (l == 0 && Enqueue<DIM>::fused_update(r) && vk == 1) {
           to_state.phi64 = r->lev[0].phi;
           to_state.mu64 = r->lev[0].mu;
           to_state.p64 = r->lev[0].p;
         }
         const int gx = (L.nx + kTileW - 1) / kTileW, gy = (L.ny + kTileH - 1) / kTileH;
-        jl.add(TileJob<float>{Lb, r->lev32[l + 1], k32(r), to_state, r->st, np2, np2, 0, 1, 0, gx}, gx * gy);
+        jl.add(TileJob<float>{Lb, r->lev32[l + 1], k32(r), to_state, gate(r), np2, np2, 0, 1, 0, gx}, gx * gy);
       }
       tiles(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, s);
       return;
@@ -1761,7 +1825,7 @@ struct BatchStep {
     if (nu2 == 0) {
       JobList<PairJob> jl;
       runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
-        jl.add(PairJob{L, C, k32(r), Level<double>{}, r->st}, nblocks(L.ncell));
+        jl.add(PairJob{L, C, k32(r), Level<double>{}, gate(r)}, nblocks(L.ncell));
       });
       go(CHHS_K_PROLONG, jl, kb_prolong<DIM>, kBlock, 0, s);
       return;
@@ -1771,9 +1835,9 @@ struct BatchStep {
         JobList<SmoothCJob> jl;
         const int pro = it == 0 ? (colour == 0 ? 1 : 2) : 0;
         runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
-          const bool upd = l == 0 && Enqueue<DIM>::fused_update(r) && it == nu2 - 1 && colour == 1;
+          const bool upd = l == 0 && Enqueue<DIM>::fused_update(r) && vk == 1 && it == nu2 - 1 && colour == 1;
           const int threads = ((L.nx + 1) / 2) * L.ny * L.nz;
-          jl.add(SmoothCJob{L, C, upd ? r->lev[0] : Level<double>{}, k32(r), r->st, colour, 0, pro},
+          jl.add(SmoothCJob{L, C, upd ? r->lev[0] : Level<double>{}, k32(r), gate(r), colour, 0, pro},
                  (threads + kSmoothBlock - 1) / kSmoothBlock);
         });
         go(l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, jl, kb_smooth_c<DIM>, kSmoothBlock, 0, s);
@@ -1791,9 +1855,14 @@ struct BatchStep {
     capture = false;
     setup(nullptr);
     coefs(nullptr);
-    norm(nullptr, 0, 0);
-    vcycle(nullptr);
-    norm(nullptr, 0, 1);
+    norm(nullptr, false, 0);
+    for (vk = n_if() + 1; vk >= 1; --vk) {
+      vstart[vk] = offs.size();
+      vcycle(nullptr);
+    }
+    vk = 1;
+    vstart[0] = offs.size();
+    norm(nullptr, false, 1);
     advance(nullptr);
   }
 
@@ -1837,10 +1906,10 @@ struct BatchStep {
     capture = true;
     cur = 0;
     struct CaptureRes {
-      cudaStream_t s[3 + kBranches] = {};
+      cudaStream_t s[4 + kBranches] = {};
       cudaEvent_t e[3 + kBranches] = {};
       ~CaptureRes() {
-        for (int q : {1, 0}) {
+        for (int q : {3, 1, 0}) {
           cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
           if (s[q] && cudaStreamIsCapturing(s[q], &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
             cudaGraph_t g = nullptr;
@@ -1855,15 +1924,15 @@ struct BatchStep {
         cudaGetLastError();
       }
     } res;
-    for (int q = 0; q < 3 + kBranches; ++q) BCU(cudaStreamCreateWithFlags(&res.s[q], cudaStreamNonBlocking));
+    for (int q = 0; q < 4 + kBranches; ++q) BCU(cudaStreamCreateWithFlags(&res.s[q], cudaStreamNonBlocking));
     for (int q = 0; q < 3 + kBranches; ++q) BCU(cudaEventCreateWithFlags(&res.e[q], cudaEventDisableTiming));
-    cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2];
+    cudaStream_t cs = res.s[0], cs2 = res.s[1], cs3 = res.s[2], cs4 = res.s[3 + kBranches];
     for (int q = 0; q < kBranches; ++q) {
       branch[q] = res.s[3 + q];
       join_ev[q] = res.e[3 + q];
     }
     fork_ev = res.e[2];
-    int n_frame = 0, n_v = 0;
+    int n_frame = 0, n_v = 0, n_other = 0;
     BCU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     counter = &n_frame;
     setup(cs);
@@ -1878,7 +1947,7 @@ struct BatchStep {
     BCU(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps));
     cudaGraphConditionalHandle cond;
     BCU(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
-    norm(cs, cond, 0);
+    norm(cs, true, 0);
     BCU(cudaStreamWaitEvent(cs, res.e[1], 0));
     BCU(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps));
     cudaGraphNodeParams cp{};
@@ -1891,9 +1960,35 @@ struct BatchStep {
     BCU(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     BCU(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    // the loop body as in a single run's graph: IF (some run takes a 3rd
+    // V-cycle) V-cycle 3; IF (a 2nd) V-cycle 2; V-cycle 1 with the update;
+    // the norms, whose last report sets the three conditions
+    BatchConds hc{};
+    hc.loop = cond;
+    hc.nif = n_if();
+    for (vk = n_if() + 1; vk >= 2; --vk) {
+      cudaGraph_t bg = nullptr;
+      BCU(cudaStreamGetCaptureInfo(cs2, &cst, nullptr, &bg, &deps, nullptr, &ndeps));
+      BCU(cudaGraphConditionalHandleCreate(&hc.cif[vk - 2], bg, 0, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams ip{};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hc.cif[vk - 2];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t ifn;
+      BCU(cudaGraphAddNode(&ifn, bg, deps, nullptr, ndeps, &ip));
+      BCU(cudaStreamUpdateCaptureDependencies(cs2, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t ib = ip.conditional.phGraph_out[0];
+      BCU(cudaStreamBeginCaptureToGraph(cs4, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      counter = &n_other;
+      vcycle(cs4);
+      BCU(cudaStreamEndCapture(cs4, &ib));
+    }
+    vk = 1;
     counter = &n_v;
     vcycle(cs2);
-    norm(cs2, cond, 1);
+    counter = &n_other;
+    norm(cs2, true, 1);
     BCU(cudaStreamEndCapture(cs2, &body));
     counter = &n_frame;
     advance(cs);
@@ -1903,6 +1998,7 @@ struct BatchStep {
     BCU(cudaGraphInstantiate(&b->exec, b->graph, 0));
     b->launches_per_v = n_v;
     b->launches_per_step = n_frame;
+    BCU(cudaMemcpy(b->d_conds, &hc, sizeof(hc), cudaMemcpyHostToDevice));
     return CHHS_OK;
   }
 
@@ -1916,16 +2012,20 @@ struct BatchStep {
     cudaStream_t s = b->stream;
     setup(s);
     coefs(s);
-    norm(s, 0, 0);
-    const size_t vcycle_cur = cur;
+    norm(s, false, 0);
     for (int v = 0;; ++v) {
-      unsigned int go_host = 0;
-      BCU(cudaMemcpyAsync(&go_host, b->d_ticket + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+      unsigned int any[3] = {0u, 0u, 0u};  // some run iterating, taking a 2nd, a 3rd V-cycle
+      BCU(cudaMemcpyAsync(any, b->d_ticket + 1, sizeof(any), cudaMemcpyDeviceToHost, s));
       BCU(cudaStreamSynchronize(s));
-      if (!go_host) break;
-      cur = vcycle_cur;
-      vcycle(s);
-      norm(s, 0, 1);
+      if (!any[0]) break;
+      for (vk = n_if() + 1; vk >= 1; --vk) {
+        if (vk > 1 && !any[vk - 1]) continue;
+        cur = vstart[vk];
+        vcycle(s);
+      }
+      vk = 1;
+      cur = vstart[0];
+      norm(s, false, 1);
     }
     cur = offs.size() - 2;  // the advance's jobs and prefix sum come last
     advance(s);
@@ -1951,7 +2051,7 @@ void batch_free(chhs_batch_t* b) {
 
 // Bytes of the batch's own bookkeeping after the runs' hierarchies.
 size_t batch_misc_bytes(int nruns) {
-  return align_up(sizeof(DevState*) * nruns) + align_up(sizeof(unsigned int)) +
+  return align_up(sizeof(DevState*) * nruns) + align_up(4 * sizeof(unsigned int)) + align_up(sizeof(BatchConds)) +
          align_up((2 * sizeof(int) + sizeof(double)) * nruns);
 }
 
@@ -2033,15 +2133,17 @@ chhs_status chhs_batch_create(int nruns, const chhs_run_desc* runs, const chhs_o
   char* misc = b->arena + (total - batch_misc_bytes(nruns));
   b->d_sts = reinterpret_cast<DevState**>(misc);
   misc += align_up(sizeof(DevState*) * nruns);
-  b->d_ticket = reinterpret_cast<unsigned int*>(misc);
-  misc += align_up(sizeof(unsigned int));
+  b->d_ticket = reinterpret_cast<unsigned int*>(misc);  // ticket, then the three "any run" flags
+  misc += align_up(4 * sizeof(unsigned int));
+  b->d_conds = reinterpret_cast<BatchConds*>(misc);
+  misc += align_up(sizeof(BatchConds));
   b->d_out = reinterpret_cast<int*>(misc);
   std::vector<DevState*> sts;
   for (chhs_t* r : b->runs) sts.push_back(r->st);
   chhs_status s = CHHS_OK;
   const size_t out_bytes = (2 * sizeof(int) + sizeof(double)) * nruns;
   if (cudaMemcpy(b->d_sts, sts.data(), sizeof(DevState*) * nruns, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(b->d_ticket, 0, 2 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(b->d_ticket, 0, 4 * sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&b->h_out, out_bytes) != cudaSuccess)
     s = CHHS_ERR_CUDA;
   if (s == CHHS_OK) {
@@ -2076,7 +2178,8 @@ chhs_status chhs_batch_step(chhs_batch_t* b, int nsteps, int* status_out, int* v
   b->err.clear();
   const int n = b->nruns;
   const double tol_max = tol_max_of(b->opts);
-  kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max, b->opts.max_v);
+  kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max, b->opts.max_v,
+                                                    b->opts.max_inner);
   BCU(cudaGetLastError());
   for (int k = 0; k < nsteps; ++k) BCU(cudaGraphLaunch(b->exec, b->stream));
   int* d_status = b->d_out;
@@ -2117,7 +2220,8 @@ chhs_status chhs_batch_profile_step(chhs_batch_t* b, double* ms_out, long long* 
   if (!b || !ms_out || !launches_out) return bfail(b, CHHS_ERR_INVALID_ARG, "NULL argument");
   b->err.clear();
   const int n = b->nruns;
-  kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max_of(b->opts), b->opts.max_v);
+  kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max_of(b->opts), b->opts.max_v,
+                                                    b->opts.max_inner);
   BCU(cudaGetLastError());
   Prof prof;
   chhs_status s;

@@ -8,7 +8,9 @@
 // is the same device function, with the same arguments and block index, as
 // in the run's own graph, so a run computes bit for bit what it computes
 // alone.  A job whose run has stopped iterating (converged, or failed) is
-// skipped by its blocks (gate: the run's loop flag).
+// skipped by its blocks (gate: one of the run's loop flags -- go for the
+// V-cycle that ends an iteration, go2 / go3 for the extra V-cycles a run
+// takes before it when its norm predicted them, DevState::inner).
 #pragma once
 #include "chhs_corr3.cuh"
 #include "chhs_kernels.cuh"
@@ -43,9 +45,9 @@ __device__ __forceinline__ const J& job_in_smem(const J* jobs, int j) {
   return *reinterpret_cast<const J*>(buf);
 }
 
-// A run still iterating in the V-cycle loop (its norm kernel set go).
-__device__ __forceinline__ bool gate_open(const DevState* gate) {
-  return gate == nullptr || *(volatile const int*)&gate->go != 0;
+// A run still iterating in the V-cycle loop (its norm kernel set the flag).
+__device__ __forceinline__ bool gate_open(const int* gate) {
+  return gate == nullptr || *(volatile const int*)gate != 0;
 }
 
 struct SetupJob {
@@ -112,14 +114,24 @@ struct NormJob {
 // iterating" (also written to any_out for the host-driven profiling path).
 // One atomic per run rather than per block: a launch over hundreds of runs
 // has hundreds of thousands of blocks.
+// any_out[0..2]: some run iterating, some run taking a 2nd, a 3rd V-cycle in
+// its next iteration; cc (device memory, written once the step graph is
+// built; null outside the graph) the loop's condition and the nif IF nodes
+// of those V-cycles.
+struct BatchConds {
+  cudaGraphConditionalHandle loop;
+  cudaGraphConditionalHandle cif[2];
+  int nif;
+};
+
 __device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njobs, bool reports,
-                                                    unsigned int* ticket, cudaGraphConditionalHandle cond,
+                                                    unsigned int* ticket, const BatchConds* cc,
                                                     unsigned int* any_out) {
   __shared__ bool last_run;
-  __shared__ int any_go;
+  __shared__ int any_go[3];
   if (threadIdx.x == 0) {
     last_run = false;
-    any_go = 0;
+    any_go[0] = any_go[1] = any_go[2] = 0;
     if (reports) {
       __threadfence();
       last_run = atomicAdd(ticket, 1u) == (unsigned)njobs - 1;
@@ -128,14 +140,24 @@ __device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njo
   __syncthreads();
   if (!last_run) return;
   __threadfence();
-  int go = 0;
-  for (int q = threadIdx.x; q < njobs; q += blockDim.x) go |= __ldcg(&jobs[q].st->go);
-  if (go) any_go = 1;
+  int go = 0, go2 = 0, go3 = 0;
+  for (int q = threadIdx.x; q < njobs; q += blockDim.x) {
+    go |= __ldcg(&jobs[q].st->go);
+    go2 |= __ldcg(&jobs[q].st->go2);
+    go3 |= __ldcg(&jobs[q].st->go3);
+  }
+  if (go) any_go[0] = 1;
+  if (go2) any_go[1] = 1;
+  if (go3) any_go[2] = 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    *any_out = any_go ? 1u : 0u;
-    if (cond) cudaGraphSetConditional(cond, any_go ? 1u : 0u);
+    for (int q = 0; q < 3; ++q) any_out[q] = any_go[q] ? 1u : 0u;
+    if (cc) {
+      cudaGraphSetConditional(cc->loop, any_go[0] ? 1u : 0u);
+      if (cc->nif >= 1) cudaGraphSetConditional(cc->cif[0], any_go[1] ? 1u : 0u);
+      if (cc->nif >= 2) cudaGraphSetConditional(cc->cif[1], any_go[2] ? 1u : 0u);
+    }
   }
 }
 
@@ -144,33 +166,32 @@ __device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njo
 // that run's decision.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) kb_norm_mixed(const NormJob* jobs, const int* start, int njobs,
-                                                        unsigned int* ticket, cudaGraphConditionalHandle cond,
-                                                        int mode, unsigned int* any_out) {
+                                                        unsigned int* ticket, const BatchConds* cc, int mode,
+                                                        unsigned int* any_out) {
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
   const NormJob& J = job_in_smem(jobs, j);
   const int lb = blockIdx.x - start[j];
   bool reports = lb == 0;
-  if (mode == 0 || gate_open(J.st))
+  if (mode == 0 || gate_open(&J.st->go))
     reports = norm_mixed_body<DIM>(lb, start[j + 1] - start[j], J.L, J.K, J.G, J.partials, J.st, 0, mode, 0);
-  batch_norm_epilogue(jobs, njobs, reports, ticket, cond, any_out);
+  batch_norm_epilogue(jobs, njobs, reports, ticket, cc, any_out);
 }
 
 // The same with the double-single residual (chhs_norm_df.cuh).
 template <int DIM>
 __global__ void __launch_bounds__(kNdfTX * kNdfTY) kb_norm_mixed_df(const NormJob* jobs, const int* start, int njobs,
-                                                                  unsigned int* ticket,
-                                                                  cudaGraphConditionalHandle cond, int mode,
-                                                                  unsigned int* any_out) {
+                                                                  unsigned int* ticket, const BatchConds* cc,
+                                                                  int mode, unsigned int* any_out) {
   pdl_enter();
   const int j = job_of(start, njobs, blockIdx.x);
   const NormJob& J = job_in_smem(jobs, j);
   const int lb = blockIdx.x - start[j];
   bool reports = lb == 0;
-  if (mode == 0 || gate_open(J.st))
+  if (mode == 0 || gate_open(&J.st->go))
     reports = norm_mixed_df_body<DIM>(lb, start[j + 1] - start[j], J.L, J.Kdf, J.K, J.f64_per8, J.G, J.partials,
                                       J.st, 0, mode, 0);
-  batch_norm_epilogue(jobs, njobs, reports, ticket, cond, any_out);
+  batch_norm_epilogue(jobs, njobs, reports, ticket, cc, any_out);
 }
 
 template <typename T>
@@ -178,7 +199,7 @@ struct TileJob {
   Level<T> L, C;
   Coefs<T> K;
   TileOut<T> out;
-  const DevState* gate;
+  const int* gate;
   int npass, halo, rhs, prolong, restrict_out;
   int gx;  // tiles per row of the level
 };
@@ -198,7 +219,7 @@ template <typename T>
 struct TailJob {
   Tail<T> tl;
   Coefs<T> K;
-  const DevState* gate;
+  const int* gate;
 };
 
 // One block per job.
@@ -214,7 +235,7 @@ struct SmoothCJob {
   Level<float> L, C;
   Level<double> U;
   Coefs<float> K;
-  const DevState* gate;
+  const int* gate;
   int colour, rhs, pro;
 };
 
@@ -233,7 +254,7 @@ struct PairJob {
   Level<float> F, C;
   Coefs<float> K;
   Level<double> U;
-  const DevState* gate;
+  const int* gate;
 };
 
 template <int DIM>
@@ -285,16 +306,19 @@ static __global__ void __launch_bounds__(kBlock) kb_advance(const AdvanceJob* jo
 }
 
 // The start of a batched call: every run's counters reset (one thread per run).
-static __global__ void kb_reset(DevState* const* sts, int nruns, double tol, double tol_max, int max_v) {
+static __global__ void kb_reset(DevState* const* sts, int nruns, double tol, double tol_max, int max_v,
+                                int max_inner) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nruns) return;
   DevState* st = sts[r];
   st->failed = 0;
   st->vtotal = 0;
   st->steps_done = 0;
+  st->checks = 0;
   st->tol = tol;
   st->tol_max = tol_max;
   st->max_v = max_v;
+  st->max_inner = max_inner;
 }
 
 // Every run's outcome of a call: status, V-cycles (as chhs_wait reports

@@ -78,7 +78,21 @@ struct DevState {
   double diag[8];  // reduction results (mass, energies)
   unsigned int ticket;  // blocks of the norm kernel that have finished
   unsigned int pad_;
+  // V-cycles between two stopping norms (loop_decision): the iteration about
+  // to run does `inner` of them (1 .. max_inner); rho is the measured
+  // contraction per V-cycle, rprev the previous norm.
+  int inner;
+  int go2, go3;    // go and inner >= 2 (>= 3): the batched step's gates of the extra V-cycles
+  int max_inner;   // 0 or 1: a norm after every V-cycle
+  int checks;      // stopping norms after V-cycles in the current call
+  int use_if;      // IF nodes of cond_if in the step graph (0, 1 or 2)
+  double rho;
+  double rprev;
+  cudaGraphConditionalHandle cond_if[2];  // IF nodes: a 2nd and a 3rd V-cycle in the iteration
 };
+
+// Most V-cycles between two stopping norms.
+constexpr int kMaxInner = 3;
 
 // chi(a, b) = (a^2 + b^2)(a + b) / 4 (Eq. 2.4) and d chi / d a.
 template <typename T>
@@ -893,6 +907,21 @@ __device__ __forceinline__ void sum_partials(const double* partials, int nparts,
 // start of a step (records r0); mode 1: after a V-cycle (counts it).  The
 // step is converged when r <= tol and rmax <= tol_max.  Returns 1 while
 // another cycle is due.
+// V-cycles for the next iteration of the step's loop: the number the
+// measured contraction rho predicts the norms (r against tol, the pointwise
+// rmax against tol_max) still need, rounded down so that no V-cycle runs past
+// the stopping point while the prediction holds; at least 1, at most
+// max_inner and the V-cycles left under max_v.  Every stop is still decided
+// by a norm of the iterate.
+__device__ __forceinline__ int next_inner(const DevState* st, double r, double rmax) {
+  const int cap = min(st->max_inner, st->max_v - st->vcycles);
+  if (cap <= 1 || !(st->rho > 0.0 && st->rho < 1.0)) return 1;
+  const double lr = log(st->rho);
+  double need = r > st->tol ? log(st->tol / r) / lr : 0.0;
+  if (rmax > st->tol_max) need = fmax(need, log(st->tol_max / rmax) / lr);
+  return max(1, min(cap, (int)floor(need)));
+}
+
 __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, double rmax, int mode) {
   st->resid = r;
   st->rmax = rmax;
@@ -907,7 +936,13 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, do
       else
         go = above ? 1u : 0u;
     } else {
-      st->vcycles += 1;
+      const int ran = max(st->inner, 1);
+      st->vcycles += ran;
+      st->checks += 1;
+      // contraction per V-cycle over the iteration just finished (kept across
+      // steps: the next step's first iteration starts from it)
+      if (st->rprev > 0.0 && r > 0.0 && isfinite(r))
+        st->rho = fmin(fmax(pow(r / st->rprev, 1.0 / ran), 1e-3), 0.9);
       bool finite = isfinite(r);
       if (!finite || r > 1e8 * (st->r0 + 1.0)) {
         st->failed = 5;  // CHHS_ERR_DIVERGED
@@ -917,6 +952,10 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, do
       }
     }
   }
+  st->rprev = r;
+  st->inner = go ? next_inner(st, r, rmax) : 1;
+  st->go2 = go && st->inner >= 2 ? 1 : 0;
+  st->go3 = go && st->inner >= 3 ? 1 : 0;
   st->go = (int)go;
   return go;
 }
@@ -955,7 +994,11 @@ __device__ __forceinline__ void norm_finish(const double* partials, int nparts, 
   st->ticket = 0;
   st->pmean = tot[1] / ncell;
   unsigned int go = loop_decision(st, sqrt(tot[0] / ncell), mx, mode);
-  if (use_cond) cudaGraphSetConditional(cond, go);
+  if (use_cond) {
+    cudaGraphSetConditional(cond, go);
+    if (st->use_if >= 1) cudaGraphSetConditional(st->cond_if[0], st->inner >= 2 ? 1u : 0u);
+    if (st->use_if >= 2) cudaGraphSetConditional(st->cond_if[1], st->inner >= 3 ? 1u : 0u);
+  }
 }
 
 // Blocks per SM of the norm kernels; their threads loop over cells with the

@@ -310,16 +310,16 @@ __device__ __forceinline__ void tile_body(int bx, int by, const Level<T>& L, con
   }
 }
 
-// gate (nullable): the run's loop state; the launch does nothing once the
+// gate (nullable): the run's loop flag; the launch does nothing once the
 // run has stopped iterating (a run of a batch that has converged).
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Level<T> L,
                                                       const __grid_constant__ Level<T> Cl, Coefs<T> K, int npass,
                                                       int halo, int rhs, int prolong, int restrict_out,
-                                                      const __grid_constant__ TileOut<T> out, const DevState* gate,
+                                                      const __grid_constant__ TileOut<T> out, const int* gate,
                                                       int tw, int th) {
   pdl_enter();
-  if (gate && *(volatile const int*)&gate->go == 0) return;
+  if (gate && *(volatile const int*)gate == 0) return;
   tile_body<T, CORR>(blockIdx.x, blockIdx.y, L, Cl, K, npass, halo, rhs, prolong, restrict_out, out, tw, th);
 }
 

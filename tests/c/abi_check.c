@@ -25,7 +25,8 @@ int main(void) {
 
     check(chhs_default_opts(&o) == CHHS_OK, "default opts");
     check(o.nu1 == 2 && o.nu2 == 2 && o.coarsest == 2 && o.tol == 1e-10 && o.precision == 0 &&
-              o.max_factor == 50.0, "default values");
+              o.max_factor == 50.0 && o.coarsest_f64 == 0 && o.f64_residual == 0 && o.max_inner == 3,
+          "default values");
     check(chhs_default_opts(NULL) == CHHS_ERR_INVALID_ARG, "default opts NULL");
 
     w2 = chhs_workspace_bytes(2, n2, NULL);

@@ -31,10 +31,13 @@ def _phi0(shape, q):
     return inputs.spinodal(shape, 500 + q, mean=-0.05, amplitude=0.3)
 
 
+@pytest.mark.parametrize("max_inner", [3, 1])
 @pytest.mark.parametrize("runs", [RUNS_2D, RUNS_3D], ids=["2d", "3d"])
-def test_batch_bit_identical_to_solo_runs(runs):
+def test_batch_bit_identical_to_solo_runs(runs, max_inner):
+    """Each run takes the V-cycles its own norms ask for (up to max_inner
+    between two norms), as it would alone."""
     nsteps = 4
-    with chhs.Batch(runs) as b:
+    with chhs.Batch(runs, opts=chhs.default_opts(precision=1, max_inner=max_inner)) as b:
         for q, r in enumerate(runs):
             b.runs[q].set_phi(_phi0(r[0], q))
         st, vb, _ = b.step(nsteps)
@@ -42,7 +45,7 @@ def test_batch_bit_identical_to_solo_runs(runs):
         per_v, per_step = b.launch_counts()
         batched = [b.runs[q].get_state() for q in range(len(runs))]
     for q, (shape, h, eps, gamma, dt) in enumerate(runs):
-        with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=1)) as solo:
+        with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=1, max_inner=max_inner)) as solo:
             solo.set_phi(_phi0(shape, q))
             _, vs, _ = solo.step(nsteps)
             ref = solo.get_state()

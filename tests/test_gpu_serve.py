@@ -74,3 +74,21 @@ def test_admission_by_memory_and_oom():
         res = sv.result(big)
         assert res["status"] == chhs.CHHS_ERR_OOM
         assert np.isnan(res["phi"]).all()  # refused at admission: it never held a state
+
+
+def test_serving_stream_through_the_request_loop():
+    """The serving workload's generator and driver (the serving study and the
+    bench's served leg): a short stream of its runs, submitted as Poisson
+    arrivals, all converge and the summary's latencies and throughput are
+    consistent with the per-run records."""
+    from paper_1611_02967_gb300 import experiments as ex
+    runs, u = ex.serving_runs(6, steps=(2, 4))
+    res, span = ex.serve(runs, ex.serve_arrivals(runs, u, 2e9))
+    assert len(res) == 6 and all(x["status"] == 0 for x in res)
+    for x in res:
+        assert x["t_submit"] <= x["t_admit"] <= x["t_done"]
+    s = ex.serving_summary(runs, res, span, 0.8)
+    assert s["all_converged"] and s["runs"] == 6
+    assert 0 < s["p50_s"] <= s["p99_s"] <= s["max_s"] <= span + 1e-9
+    work = sum(r["cells"] * r["steps"] for r in runs)
+    assert abs(s["value"] * span - work) <= 1e-6 * work
