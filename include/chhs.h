@@ -77,7 +77,7 @@ typedef struct {
     int max_inner;     /* most V-cycles between two stopping norms, 1..3 (default 3; otherwise
                           CHHS_ERR_INVALID_ARG).  After each norm the device predicts, from the
                           contraction per V-cycle it has measured, how many V-cycles the norm
-                          still needs to reach tol (rounded down, at least 1, at most max_inner)
+                          still needs to reach tol (rounded to the nearest, at least 1, at most max_inner)
                           and runs that many before the next norm; in the mixed form they are
                           the correction V-cycles of one defect-correction iteration.  A step
                           still ends only on a norm at or below tol.  1: a norm after every
