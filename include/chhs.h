@@ -74,7 +74,7 @@ typedef struct {
                           single-precision pipes, which run 64 times faster on GB300.  Either
                           way the stopping norm is that of the double-precision iterate.  Not 0
                           or 1: CHHS_ERR_INVALID_ARG. */
-    int max_inner;     /* most V-cycles between two stopping norms, 1..3 (default 3; otherwise
+    int max_inner;     /* most V-cycles between two stopping norms, 1..4 (default 3; otherwise
                           CHHS_ERR_INVALID_ARG).  After each norm the device predicts, from the
                           contraction per V-cycle it has measured, how many V-cycles the norm
                           still needs to reach tol (rounded to the nearest, at least 1, at most max_inner)

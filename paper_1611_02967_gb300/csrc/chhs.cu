@@ -671,11 +671,12 @@ struct Enqueue {
     CU(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    // the loop body: IF (inner >= 3) V-cycle; IF (inner >= 2) V-cycle; the
-    // V-cycle with the update; the stopping norm, which sets the loop
-    // condition and the two IF conditions for the next iteration
+    // the loop body: IF (inner >= 4) V-cycle; IF (inner >= 3) V-cycle; IF
+    // (inner >= 2) V-cycle; the V-cycle with the update; the stopping norm,
+    // which sets the loop condition and the IF conditions for the next
+    // iteration
     const int n_if = std::min(run->opts.max_inner, kMaxInner) - 1;
-    cudaGraphConditionalHandle cif[2] = {0, 0};
+    cudaGraphConditionalHandle cif[kMaxInner - 1] = {};
     for (int q = n_if - 1; q >= 0; --q) {
       cudaGraph_t bg = nullptr;
       CU(cudaStreamGetCaptureInfo(cs2, &cst, nullptr, &bg, &deps, nullptr, &ndeps));
@@ -707,12 +708,9 @@ struct Enqueue {
     run->launches_per_v = n_v;
     run->launches_per_step = n_frame;
     // the IF nodes' handles, for the norm kernels that set them
-    struct {
-      int use_if;
-      cudaGraphConditionalHandle h[2];
-    } ifs{std::max(n_if, 0), {cif[0], cif[1]}};
-    CU(cudaMemcpyAsync(&run->st->use_if, &ifs.use_if, sizeof(int), cudaMemcpyHostToDevice, run->stream));
-    CU(cudaMemcpyAsync(run->st->cond_if, ifs.h, sizeof(ifs.h), cudaMemcpyHostToDevice, run->stream));
+    const int use_if = std::max(n_if, 0);
+    CU(cudaMemcpyAsync(&run->st->use_if, &use_if, sizeof(int), cudaMemcpyHostToDevice, run->stream));
+    CU(cudaMemcpyAsync(run->st->cond_if, cif, sizeof(cif), cudaMemcpyHostToDevice, run->stream));
     CU(cudaStreamSynchronize(run->stream));
     return CHHS_OK;
   }
@@ -959,7 +957,7 @@ chhs_status chhs_default_opts(chhs_opts* o) {
   o->max_factor = 50.0;
   o->coarsest_f64 = 0;
   o->f64_residual = 0;
-  o->max_inner = kMaxInner;
+  o->max_inner = 3;  // kMaxInner (4) measured no faster on the benchmark workloads
   return CHHS_OK;
 }
 
@@ -1562,12 +1560,13 @@ struct BatchStep {
   chhs_batch_t* b;
   bool capture = false;
   // the V-cycle being emitted: 1 ends an iteration (gate go, with the
-  // update u <- u + e), 2 and 3 are the extra V-cycles before it (gates go2,
-  // go3, no update) that a run takes when its norm predicted them
+  // update u <- u + e), 2 .. kMaxInner are the extra V-cycles before it
+  // (gates go_more[vk - 2], no update) that a run takes when its norm
+  // predicted them
   int vk = 1;
-  const int* gate(const chhs_t* r) const { return vk == 1 ? &r->st->go : vk == 2 ? &r->st->go2 : &r->st->go3; }
+  const int* gate(const chhs_t* r) const { return vk == 1 ? &r->st->go : &r->st->go_more[vk - 2]; }
   int n_if() const { return std::min(b->opts.max_inner, kMaxInner) - 1; }
-  size_t vstart[kMaxInner + 1] = {};  // table positions of the V-cycles vk = 1..3 and the norm after them (plan)
+  size_t vstart[kMaxInner + 1] = {};  // table positions of the V-cycles vk = 1..kMaxInner and the norm after them (plan)
   std::vector<char> buf;            // host image of the job tables
   std::vector<size_t> offs;         // table offsets in emission order
   size_t cur = 0;
@@ -1909,7 +1908,7 @@ struct BatchStep {
       cudaStream_t s[4 + kBranches] = {};
       cudaEvent_t e[3 + kBranches] = {};
       ~CaptureRes() {
-        for (int q : {3, 1, 0}) {
+        for (int q : {3 + kBranches, 1, 0}) {  // the IF bodies', the loop body's, the step's capture
           cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
           if (s[q] && cudaStreamIsCapturing(s[q], &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
             cudaGraph_t g = nullptr;
@@ -1960,9 +1959,9 @@ struct BatchStep {
     BCU(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     BCU(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    // the loop body as in a single run's graph: IF (some run takes a 3rd
-    // V-cycle) V-cycle 3; IF (a 2nd) V-cycle 2; V-cycle 1 with the update;
-    // the norms, whose last report sets the three conditions
+    // the loop body as in a single run's graph: IF (some run takes a 4th
+    // V-cycle) V-cycle 4; ... IF (a 2nd) V-cycle 2; V-cycle 1 with the
+    // update; the norms, whose last report sets the conditions
     BatchConds hc{};
     hc.loop = cond;
     hc.nif = n_if();
@@ -2014,7 +2013,7 @@ struct BatchStep {
     coefs(s);
     norm(s, false, 0);
     for (int v = 0;; ++v) {
-      unsigned int any[3] = {0u, 0u, 0u};  // some run iterating, taking a 2nd, a 3rd V-cycle
+      unsigned int any[kMaxInner] = {};  // some run iterating, taking a 2nd, 3rd, ... V-cycle
       BCU(cudaMemcpyAsync(any, b->d_ticket + 1, sizeof(any), cudaMemcpyDeviceToHost, s));
       BCU(cudaStreamSynchronize(s));
       if (!any[0]) break;
@@ -2051,7 +2050,8 @@ void batch_free(chhs_batch_t* b) {
 
 // Bytes of the batch's own bookkeeping after the runs' hierarchies.
 size_t batch_misc_bytes(int nruns) {
-  return align_up(sizeof(DevState*) * nruns) + align_up(4 * sizeof(unsigned int)) + align_up(sizeof(BatchConds)) +
+  return align_up(sizeof(DevState*) * nruns) + align_up((1 + kMaxInner) * sizeof(unsigned int)) +
+         align_up(sizeof(BatchConds)) +
          align_up((2 * sizeof(int) + sizeof(double)) * nruns);
 }
 
@@ -2133,8 +2133,8 @@ chhs_status chhs_batch_create(int nruns, const chhs_run_desc* runs, const chhs_o
   char* misc = b->arena + (total - batch_misc_bytes(nruns));
   b->d_sts = reinterpret_cast<DevState**>(misc);
   misc += align_up(sizeof(DevState*) * nruns);
-  b->d_ticket = reinterpret_cast<unsigned int*>(misc);  // ticket, then the three "any run" flags
-  misc += align_up(4 * sizeof(unsigned int));
+  b->d_ticket = reinterpret_cast<unsigned int*>(misc);  // ticket, then the kMaxInner "any run" flags
+  misc += align_up((1 + kMaxInner) * sizeof(unsigned int));
   b->d_conds = reinterpret_cast<BatchConds*>(misc);
   misc += align_up(sizeof(BatchConds));
   b->d_out = reinterpret_cast<int*>(misc);
@@ -2143,7 +2143,7 @@ chhs_status chhs_batch_create(int nruns, const chhs_run_desc* runs, const chhs_o
   chhs_status s = CHHS_OK;
   const size_t out_bytes = (2 * sizeof(int) + sizeof(double)) * nruns;
   if (cudaMemcpy(b->d_sts, sts.data(), sizeof(DevState*) * nruns, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(b->d_ticket, 0, 4 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(b->d_ticket, 0, (1 + kMaxInner) * sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&b->h_out, out_bytes) != cudaSuccess)
     s = CHHS_ERR_CUDA;
   if (s == CHHS_OK) {

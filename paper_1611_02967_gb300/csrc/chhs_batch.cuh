@@ -9,7 +9,7 @@
 // in the run's own graph, so a run computes bit for bit what it computes
 // alone.  A job whose run has stopped iterating (converged, or failed) is
 // skipped by its blocks (gate: one of the run's loop flags -- go for the
-// V-cycle that ends an iteration, go2 / go3 for the extra V-cycles a run
+// V-cycle that ends an iteration, go_more[] for the extra V-cycles a run
 // takes before it when its norm predicted them, DevState::inner).
 #pragma once
 #include "chhs_corr3.cuh"
@@ -114,13 +114,13 @@ struct NormJob {
 // iterating" (also written to any_out for the host-driven profiling path).
 // One atomic per run rather than per block: a launch over hundreds of runs
 // has hundreds of thousands of blocks.
-// any_out[0..2]: some run iterating, some run taking a 2nd, a 3rd V-cycle in
-// its next iteration; cc (device memory, written once the step graph is
-// built; null outside the graph) the loop's condition and the nif IF nodes
-// of those V-cycles.
+// any_out[0]: some run iterating; any_out[1 + q]: some run taking a
+// (2 + q)-th V-cycle in its next iteration.  cc (device memory, written once
+// the step graph is built; null outside the graph): the loop's condition and
+// the nif IF nodes of those V-cycles.
 struct BatchConds {
   cudaGraphConditionalHandle loop;
-  cudaGraphConditionalHandle cif[2];
+  cudaGraphConditionalHandle cif[kMaxInner - 1];
   int nif;
 };
 
@@ -128,10 +128,10 @@ __device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njo
                                                     unsigned int* ticket, const BatchConds* cc,
                                                     unsigned int* any_out) {
   __shared__ bool last_run;
-  __shared__ int any_go[3];
+  __shared__ int any_go[kMaxInner];
   if (threadIdx.x == 0) {
     last_run = false;
-    any_go[0] = any_go[1] = any_go[2] = 0;
+    for (int q = 0; q < kMaxInner; ++q) any_go[q] = 0;
     if (reports) {
       __threadfence();
       last_run = atomicAdd(ticket, 1u) == (unsigned)njobs - 1;
@@ -140,23 +140,20 @@ __device__ __forceinline__ void batch_norm_epilogue(const NormJob* jobs, int njo
   __syncthreads();
   if (!last_run) return;
   __threadfence();
-  int go = 0, go2 = 0, go3 = 0;
+  int go[kMaxInner] = {};
   for (int q = threadIdx.x; q < njobs; q += blockDim.x) {
-    go |= __ldcg(&jobs[q].st->go);
-    go2 |= __ldcg(&jobs[q].st->go2);
-    go3 |= __ldcg(&jobs[q].st->go3);
+    go[0] |= __ldcg(&jobs[q].st->go);
+    for (int m = 1; m < kMaxInner; ++m) go[m] |= __ldcg(&jobs[q].st->go_more[m - 1]);
   }
-  if (go) any_go[0] = 1;
-  if (go2) any_go[1] = 1;
-  if (go3) any_go[2] = 1;
+  for (int m = 0; m < kMaxInner; ++m)
+    if (go[m]) any_go[m] = 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    for (int q = 0; q < 3; ++q) any_out[q] = any_go[q] ? 1u : 0u;
+    for (int q = 0; q < kMaxInner; ++q) any_out[q] = any_go[q] ? 1u : 0u;
     if (cc) {
       cudaGraphSetConditional(cc->loop, any_go[0] ? 1u : 0u);
-      if (cc->nif >= 1) cudaGraphSetConditional(cc->cif[0], any_go[1] ? 1u : 0u);
-      if (cc->nif >= 2) cudaGraphSetConditional(cc->cif[1], any_go[2] ? 1u : 0u);
+      for (int q = 0; q < cc->nif; ++q) cudaGraphSetConditional(cc->cif[q], any_go[1 + q] ? 1u : 0u);
     }
   }
 }

@@ -82,17 +82,17 @@ struct DevState {
   // to run does `inner` of them (1 .. max_inner); rho is the measured
   // contraction per V-cycle, rprev the previous norm.
   int inner;
-  int go2, go3;    // go and inner >= 2 (>= 3): the batched step's gates of the extra V-cycles
+  int go_more[3];  // go and inner >= 2 + q: the batched step's gates of the extra V-cycles
   int max_inner;   // 0 or 1: a norm after every V-cycle
   int checks;      // stopping norms after V-cycles in the current call
-  int use_if;      // IF nodes of cond_if in the step graph (0, 1 or 2)
+  int use_if;      // IF nodes of cond_if in the step graph (0 .. 3)
   double rho;
   double rprev;
-  cudaGraphConditionalHandle cond_if[2];  // IF nodes: a 2nd and a 3rd V-cycle in the iteration
+  cudaGraphConditionalHandle cond_if[3];  // IF node q: a (2 + q)-th V-cycle in the iteration
 };
 
-// Most V-cycles between two stopping norms.
-constexpr int kMaxInner = 3;
+// Most V-cycles between two stopping norms (DevState::go_more, cond_if hold kMaxInner - 1).
+constexpr int kMaxInner = 4;
 
 // chi(a, b) = (a^2 + b^2)(a + b) / 4 (Eq. 2.4) and d chi / d a.
 template <typename T>
@@ -956,8 +956,7 @@ __device__ __forceinline__ unsigned int loop_decision(DevState* st, double r, do
   }
   st->rprev = r;
   st->inner = go ? next_inner(st, r, rmax) : 1;
-  st->go2 = go && st->inner >= 2 ? 1 : 0;
-  st->go3 = go && st->inner >= 3 ? 1 : 0;
+  for (int q = 0; q < kMaxInner - 1; ++q) st->go_more[q] = go && st->inner >= 2 + q ? 1 : 0;
   st->go = (int)go;
   return go;
 }
@@ -998,8 +997,7 @@ __device__ __forceinline__ void norm_finish(const double* partials, int nparts, 
   unsigned int go = loop_decision(st, sqrt(tot[0] / ncell), mx, mode);
   if (use_cond) {
     cudaGraphSetConditional(cond, go);
-    if (st->use_if >= 1) cudaGraphSetConditional(st->cond_if[0], st->inner >= 2 ? 1u : 0u);
-    if (st->use_if >= 2) cudaGraphSetConditional(st->cond_if[1], st->inner >= 3 ? 1u : 0u);
+    for (int q = 0; q < st->use_if; ++q) cudaGraphSetConditional(st->cond_if[q], st->inner >= 2 + q ? 1u : 0u);
   }
 }
 

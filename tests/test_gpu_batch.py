@@ -31,7 +31,7 @@ def _phi0(shape, q):
     return inputs.spinodal(shape, 500 + q, mean=-0.05, amplitude=0.3)
 
 
-@pytest.mark.parametrize("max_inner", [3, 1])
+@pytest.mark.parametrize("max_inner", [4, 2, 1])
 @pytest.mark.parametrize("runs", [RUNS_2D, RUNS_3D], ids=["2d", "3d"])
 def test_batch_bit_identical_to_solo_runs(runs, max_inner):
     """Each run takes the V-cycles its own norms ask for (up to max_inner

@@ -71,7 +71,7 @@ def test_create_rejects_bad_problem(L, case):
 BAD_OPTS = [dict(nu1=0, nu2=0), dict(nu1=-1), dict(nu2=-1), dict(max_v=0), dict(coarsest=0), dict(coarsest=1),
             dict(tol=0.0),
             dict(tol=-1e-10), dict(tol=NAN), dict(precision=2), dict(precision=-1), dict(max_factor=-1.0),
-            dict(max_factor=NAN), dict(max_inner=0), dict(max_inner=4)]
+            dict(max_factor=NAN), dict(max_inner=0), dict(max_inner=5)]
 
 
 @pytest.mark.parametrize("case", range(len(BAD_OPTS)))
