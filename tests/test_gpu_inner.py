@@ -70,3 +70,22 @@ def test_eager_profile_step_follows_the_inner_counts():
         acc = b.profile_step()
         assert np.max(np.abs(a.get_phi() - b.get_phi())) <= 1e-12
         assert a.norm_checks() < va or va <= 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_inner_vcycles_respect_max_v(precision):
+    """The predicted V-cycles never take a step past max_v: a step capped
+    below what it needs stops with CHHS_ERR_NOT_CONVERGED after exactly
+    max_v V-cycles (the count of the one-norm-per-V-cycle run), state kept."""
+    shape, h = (128, 128), 0.025
+    phi0 = inputs.spinodal(shape, 5, mean=0.0)
+    for max_v in (2, 4):
+        with chhs.Run(shape, h, 0.05, 1.0, 0.005,
+                      opts=chhs.default_opts(precision=precision, max_v=max_v, max_inner=4)) as run:
+            run.set_phi(phi0)
+            st, v, r = run.step(1, check=False)
+            assert st == chhs.CHHS_ERR_NOT_CONVERGED
+            assert v == max_v
+            assert r > 1e-10
+            phim, phimm1, _, _ = run.get_state()
+            assert np.array_equal(phim, phi0) and np.array_equal(phimm1, phi0)
