@@ -463,16 +463,8 @@ def bubbles_leg(stream, flush, steps=10, warmup=3):
 
 
 def batched_runs(seed=4, nruns=256):
-    """The batched workload's runs: sizes drawn from {64..1024}^2, eps
-    U(0.02,0.08), gamma U(0.5,4), h 0.025, dt 0.005, seeded spinodal data."""
-    import numpy as np
-
-    from paper_1611_02967_gb300 import inputs
-    u = inputs.uniform01(seed, nruns * 3, stream=13).reshape(nruns, 3)
-    sizes = np.array([64, 128, 256, 512, 1024])[np.minimum((u[:, 0] * 5).astype(int), 4)]
-    runs = [((int(n), int(n)), 0.025, 0.02 + 0.06 * u[k, 1], 0.5 + 3.5 * u[k, 2], 0.005) for k, n in enumerate(sizes)]
-    phis = [inputs.spinodal((int(n), int(n)), seed * 1000 + k, mean=0.0) for k, n in enumerate(sizes)]
-    return runs, phis, sizes
+    from paper_1611_02967_gb300 import experiments
+    return experiments.batched_runs(seed, nruns)
 
 
 def batched_leg(seed=4, nruns=256, steps=100, request_loop=True):

@@ -90,6 +90,20 @@ def gamma_study(gammas=(0.0, 2.0, 4.0), steps=STEPS, precision=0, sample_steps=(
     return rows, snaps
 
 
+# ---------------------------------------------------------------- batched
+
+def batched_runs(seed=4, nruns=256):
+    """The batched workload's runs: sizes drawn from {64..1024}^2, eps
+    U(0.02,0.08), gamma U(0.5,4), h 0.025, dt 0.005, seeded spinodal data.
+    Returns (run descriptions (shape, h, eps, gamma, dt), initial fields,
+    sizes)."""
+    u = inputs.uniform01(seed, nruns * 3, stream=13).reshape(nruns, 3)
+    sizes = np.array([64, 128, 256, 512, 1024])[np.minimum((u[:, 0] * 5).astype(int), 4)]
+    runs = [((int(n), int(n)), 0.025, 0.02 + 0.06 * u[k, 1], 0.5 + 3.5 * u[k, 2], 0.005) for k, n in enumerate(sizes)]
+    phis = [inputs.spinodal((int(n), int(n)), seed * 1000 + k, mean=0.0) for k, n in enumerate(sizes)]
+    return runs, phis, sizes
+
+
 # ---------------------------------------------------------------- serving
 
 SERVE_SEED = 5

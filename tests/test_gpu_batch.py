@@ -117,3 +117,31 @@ def test_batch_reports_a_failed_run_and_advances_the_others():
         solo.set_phi(good)
         solo.step(2)
         assert np.array_equal(solo.get_phi(), got)
+
+
+def test_full_batched_configuration_sampled_runs_match_oracle():
+    """The batched configuration at its full size, as the bench runs it (256
+    runs of 64^2 ... 1024^2, one chhs_batch, default options): after two
+    steps, the third step of sampled runs -- the first run of each size,
+    1024^2 included -- equals the oracle's step from the same state within
+    the mixed-precision bound, and every run converged."""
+    from paper_1611_02967_gb300 import experiments
+    runs, phis, sizes = experiments.batched_runs(4, 256)
+    sample = sorted({int(n): k for k, n in reversed(list(enumerate(sizes)))}.values())
+    assert {int(sizes[k]) for k in sample} == {64, 128, 256, 512, 1024}
+    with chhs.Batch(runs) as b:
+        for k in range(len(runs)):
+            b.runs[k].set_phi(phis[k])
+        st, _, _ = b.step(2)
+        assert all(x == chhs.CHHS_OK for x in st)
+        before = {k: b.runs[k].get_state() for k in sample}
+        st, v, r = b.step(1)
+        assert all(x == chhs.CHHS_OK for x in st) and max(r) <= 1e-10
+        after = {k: b.runs[k].get_phi() for k in sample}
+    for k in sample:
+        shape, h, eps, gamma, dt = runs[k]
+        phim, phimm1, mu, p = before[k]
+        o = oracle.step(phim, phimm1, oracle.Params(h, eps, gamma, dt, tol=1e-13, max_v=100),
+                        2.0 * phim - phimm1, mu, p)
+        assert o[5] == oracle.OK
+        assert np.max(np.abs(after[k] - o[0])) <= MIXED_TOL, (k, shape)
