@@ -470,8 +470,9 @@ def batched_runs(seed=4, nruns=256):
 def batched_leg(seed=4, nruns=256, steps=100, request_loop=True):
     """The batched workload in full (256 runs, 100 steps each, mixed
     precision) through chhs_batch: one graph of batched launches, one per
-    kernel and multigrid level over all runs, timed with CUDA events on the
-    batch's stream (creation and initial data untimed).  For comparison the
+    kernel and multigrid level over all runs, its tail size and coarse sweep
+    counts picked by chhs_batch_autotune, timed with CUDA events on the
+    batch's stream (creation, tuning and initial data untimed).  For comparison the
     same runs also go through the request loop (32 runs on per-run streams)."""
     import numpy as np
     import torch
@@ -483,6 +484,7 @@ def batched_leg(seed=4, nruns=256, steps=100, request_loop=True):
     with chhs.Batch(runs, stream=stream.cuda_stream) as b:
         for k in range(nruns):
             b.runs[k].set_phi(phis[k])
+        tune = b.autotune(2)  # untimed; every run's state is restored
         per_v, per_step = b.launch_counts()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -493,7 +495,7 @@ def batched_leg(seed=4, nruns=256, steps=100, request_loop=True):
         secs = e0.elapsed_time(e1) / 1e3
     out = {"value": work / secs, "unit": UNIT, "runs": nruns, "steps_each": steps, "seconds": secs,
            "all_converged": all(x == 0 for x in st), "vcycles_per_step": float(np.mean(v)) / steps,
-           "launches_per_vcycle": per_v, "launches_per_step_frame": per_step,
+           "launches_per_vcycle": per_v, "launches_per_step_frame": per_step, "tuning": tune,
            "sample": "%d runs (sizes drawn from {64..1024}^2, seed 4), %d steps each, one chhs_batch (mixed "
                      "precision)%s" % (nruns, steps, "; the full batched configuration" if (nruns, steps) == (256, 100)
                                        else "")}

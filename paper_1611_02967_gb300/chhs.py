@@ -31,9 +31,11 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_autotune", "chhs_batch_workspace_bytes", "chhs_batch_create", "chhs_batch_size", "chhs_batch_run",
            "chhs_batch_step", "chhs_batch_launch_counts", "chhs_batch_last_error", "chhs_batch_destroy",
            "chhs_profile_smooth32", "chhs_probe_fp64", "chhs_batch_profile_step", "chhs_set_tuning",
-           "chhs_norm_checks"]
+           "chhs_norm_checks", "chhs_batch_set_tuning", "chhs_batch_autotune"]
 
 # kernel kinds of chhs_profile_step
+kTileThreads = 512  # threads of a 2D tile (the batch's fixed tile launch)
+
 K_NAMES = ["smooth", "residual_restrict", "coarse_rhs", "prolong", "tail", "norm", "frame", "smooth_finest"]
 
 
@@ -125,6 +127,8 @@ def lib():
             "chhs_probe_fp64": (i, [_dp]),
             "chhs_batch_profile_step": (i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
             "chhs_set_tuning": (i, [_vp, ctypes.c_void_p]),
+            "chhs_batch_set_tuning": (i, [_vp, ctypes.c_void_p]),
+            "chhs_batch_autotune": (i, [_vp, i, ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -510,6 +514,24 @@ class Batch:
         a, b = ctypes.c_int(0), ctypes.c_int(0)
         lib().chhs_batch_launch_counts(self.handle, ctypes.byref(a), ctypes.byref(b))
         return a.value, b.value
+
+    def _check(self, st, what):
+        if st != CHHS_OK:
+            raise ChhsError(st, "%s: %s" % (what, lib().chhs_batch_last_error(self.handle).decode()))
+
+    def set_tuning(self, tail_cells, coarse_nu1, coarse_nu2, norm_f64_per8=3):
+        """chhs_batch_set_tuning: tail size, coarse sweep counts and the norm's
+        FP64 share for every run; rebuilds the batch's graph."""
+        t = Tuning(int(tail_cells), 0, kTileThreads, int(coarse_nu1), int(coarse_nu2), 32, 16, int(norm_f64_per8), 0.0)
+        self._check(lib().chhs_batch_set_tuning(self.handle, ctypes.byref(t)), "chhs_batch_set_tuning")
+
+    def autotune(self, trial_steps=2):
+        """chhs_batch_autotune: pick the batch's tail size and coarse sweep
+        counts by timing its own steps (every run's state is left as it was)."""
+        t = Tuning()
+        self._check(lib().chhs_batch_autotune(self.handle, int(trial_steps), ctypes.byref(t)), "chhs_batch_autotune")
+        return dict(tail_cells=t.tail_cells, coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2,
+                    norm_f64_per8=t.norm_f64_per8, ms_per_step=t.ms_per_step)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1682,12 +1682,14 @@ struct BatchStep {
 
   void vcycle(cudaStream_t s) {
     const int ts = max_tail_start();
-    const int nu1 = b->opts.nu1, nu2 = b->opts.nu2;
-    for (int l = 0; l < ts; ++l) pre(s, l, nu1);
+    // the options' sweeps on the finest level, the batch's coarse ones below
+    // (chhs_batch_set_tuning; every run of the batch has the same)
+    const chhs_t* r0 = b->runs[0];
+    for (int l = 0; l < ts; ++l) pre(s, l, l == 0 ? b->opts.nu1 : r0->nu1c);
     std::vector<TailJob<float>> tails;
     for (chhs_t* r : b->runs) tails.push_back(TailJob<float>{r->tail32, k32(r), gate(r)});
     go_tail(tails, s);
-    for (int l = ts - 1; l >= 0; --l) post(s, l, nu2);
+    for (int l = ts - 1; l >= 0; --l) post(s, l, l == 0 ? b->opts.nu2 : r0->nu2c);
     if (vk != 1) return;
     JobList<PairJob> upd;
     for (chhs_t* r : b->runs)
@@ -1872,7 +1874,7 @@ struct BatchStep {
     BCU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     for (chhs_t* r : b->runs) tail_smem = std::max(tail_smem, Enqueue<DIM>::template tail_bytes<float, true>(r->tail32));
     if (DIM == 2) {
-      const int halo = 2 * std::max(b->opts.nu1, b->opts.nu2) + 1;
+      const int halo = 2 * std::max(std::max(b->opts.nu1, b->opts.nu2), std::max(b->runs[0]->nu1c, b->runs[0]->nu2c)) + 1;
       tile_smem = tile_smem_bytes(halo, tile_nfields<true>(), sizeof(float));
     }
     auto raise_to = [&](const void* fn, size_t dyn) -> chhs_status {
@@ -2213,6 +2215,152 @@ chhs_status chhs_batch_launch_counts(const chhs_batch_t* b, int* per_vcycle, int
   if (!b || !per_vcycle || !per_step) return CHHS_ERR_INVALID_ARG;
   *per_vcycle = b->launches_per_v;
   *per_step = b->launches_per_step;
+  return CHHS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Apply a tuning to every run of the batch and rebuild its step graph.
+chhs_status batch_apply(chhs_batch_t* b, int tail_cells, int nu1c, int nu2c, int norm_f64_per8) {
+  BCU(cudaStreamSynchronize(b->stream));
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->tables) cudaFree(b->tables);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->tables = nullptr;
+  for (chhs_t* r : b->runs) {
+    r->tail_cells = tail_cells;
+    r->nu1c = nu1c;
+    r->nu2c = nu2c;
+    r->norm_f64_per8 = norm_f64_per8;
+    place_tail(r);
+  }
+  chhs_status s;
+  if (b->dim == 2) {
+    BatchStep<2> bs{b};
+    s = bs.build();
+  } else {
+    BatchStep<3> bs{b};
+    s = bs.build();
+  }
+  if (s == CHHS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) s = CHHS_ERR_CUDA;
+  cudaGetLastError();
+  return s;
+}
+
+bool batch_tuning_ok(const chhs_tuning* t) {
+  return t && t->tail_cells >= 1 && t->coarse_nu1 >= 0 && t->coarse_nu2 >= 0 &&
+         t->coarse_nu1 + t->coarse_nu2 >= 1 && t->norm_f64_per8 >= 0 && t->norm_f64_per8 <= 8;
+}
+
+}  // namespace
+
+extern "C" {
+
+chhs_status chhs_batch_set_tuning(chhs_batch_t* b, const chhs_tuning* t) {
+  if (!b) return CHHS_ERR_INVALID_ARG;
+  if (!batch_tuning_ok(t)) return bfail(b, CHHS_ERR_INVALID_ARG, "invalid tuning");
+  b->err.clear();
+  const chhs_t* r0 = b->runs[0];
+  const int keep[4] = {r0->tail_cells, r0->nu1c, r0->nu2c, r0->norm_f64_per8};
+  chhs_status s = batch_apply(b, t->tail_cells, t->coarse_nu1, t->coarse_nu2, t->norm_f64_per8);
+  if (s == CHHS_OK) return CHHS_OK;
+  const std::string why = b->err;
+  if (batch_apply(b, keep[0], keep[1], keep[2], keep[3]) != CHHS_OK) return bfail(b, CHHS_ERR_CUDA, why);
+  return bfail(b, s == CHHS_ERR_CUDA ? CHHS_ERR_CUDA : CHHS_ERR_INVALID_ARG, why);
+}
+
+chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* out) {
+  if (!b || trial_steps < 1) return bfail(b, CHHS_ERR_INVALID_ARG, "bad argument");
+  b->err.clear();
+  // every run's state (phi^m, phi^{m-1}, mu, p), restored after each trial
+  size_t total = 0;
+  for (const chhs_t* r : b->runs) total += 4 * (size_t)r->ncell();
+  double* keep = nullptr;
+  if (cudaMalloc(&keep, sizeof(double) * total) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, CHHS_ERR_OOM, "no room for the saved states");
+  }
+  auto copy_states = [&](bool save) -> bool {
+    size_t off = 0;
+    for (chhs_t* r : b->runs) {
+      const Level<double>& F = r->lev[0];
+      double* st[4] = {F.phim, r->phimm1, F.mu, F.p};
+      const size_t bytes = sizeof(double) * r->ncell();
+      for (double* a : st) {
+        if (cudaMemcpyAsync(save ? keep + off : a, save ? a : keep + off, bytes, cudaMemcpyDeviceToDevice,
+                            b->stream) != cudaSuccess)
+          return false;
+        off += r->ncell();
+      }
+    }
+    return cudaStreamSynchronize(b->stream) == cudaSuccess;
+  };
+  struct Cand {
+    int tc, n1, n2;
+  };
+  const chhs_t* r0 = b->runs[0];
+  const Cand orig{r0->tail_cells, r0->nu1c, r0->nu2c};
+  std::vector<Cand> cands;
+  std::vector<std::pair<int, int>> coarse = {{b->opts.nu1, b->opts.nu2}};
+  if (b->opts.nu1 > 1 && b->opts.nu2 > 1) coarse.push_back({1, 1});
+  for (const auto& cn : coarse)
+    for (int tc : {b->dim == 2 ? 256 : 64, b->dim == 2 ? 1024 : 512, 4096}) cands.push_back({tc, cn.first, cn.second});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  chhs_status s = CHHS_OK;
+  float best_ms = -1.f;
+  Cand best = orig;
+  if (!copy_states(true) || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    s = CHHS_ERR_CUDA;
+  for (size_t q = 0; s == CHHS_OK && q < cands.size(); ++q) {
+    const Cand& c = cands[q];
+    if (batch_apply(b, c.tc, c.n1, c.n2, r0->norm_f64_per8) != CHHS_OK) continue;  // e.g. a tail too big
+    // one untimed step (the new graph's first launch), then the timed ones,
+    // each from the saved state
+    bool ok = copy_states(false) && chhs_batch_step(b, 1, nullptr, nullptr, nullptr) == CHHS_OK && copy_states(false);
+    if (!ok) continue;
+    const int n = b->nruns;
+    kb_reset<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_sts, n, b->opts.tol, tol_max_of(b->opts), b->opts.max_v,
+                                                      b->opts.max_inner);
+    cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < trial_steps; ++k) cudaGraphLaunch(b->exec, b->stream);
+    cudaEventRecord(e1, b->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      s = CHHS_ERR_CUDA;
+      break;
+    }
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  if (s == CHHS_OK && batch_apply(b, best.tc, best.n1, best.n2, r0->norm_f64_per8) != CHHS_OK) {
+    best_ms = -1.f;  // the fastest could not be rebuilt: back to the original setting
+    if (batch_apply(b, orig.tc, orig.n1, orig.n2, r0->norm_f64_per8) != CHHS_OK) s = CHHS_ERR_CUDA;
+  }
+  if (s == CHHS_OK && !copy_states(false)) s = CHHS_ERR_CUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(keep);
+  cudaGetLastError();
+  if (s != CHHS_OK) return bfail(b, s, "autotune failed");
+  b->err.clear();  // a trial's failed candidate left its message
+  if (out) {
+    const chhs_t* r = b->runs[0];
+    out->tail_cells = r->tail_cells;
+    out->split_threads = r->split_threads;
+    out->tile_threads = kTileThreads;
+    out->coarse_nu1 = r->nu1c;
+    out->coarse_nu2 = r->nu2c;
+    out->tile_w = kTileW;
+    out->tile_h = kTileH;
+    out->norm_f64_per8 = r->norm_f64_per8;
+    out->ms_per_step = best_ms < 0.f ? -1.0 : best_ms / trial_steps;
+  }
   return CHHS_OK;
 }
 

@@ -145,3 +145,48 @@ def test_full_batched_configuration_sampled_runs_match_oracle():
                         2.0 * phim - phimm1, mu, p)
         assert o[5] == oracle.OK
         assert np.max(np.abs(after[k] - o[0])) <= MIXED_TOL, (k, shape)
+
+
+@pytest.mark.parametrize("runs", [RUNS_2D[:4], RUNS_3D[:2]], ids=["2d", "3d"])
+def test_batch_tuning_matches_solo_runs_with_the_same_tuning(runs):
+    """chhs_batch_set_tuning: the batch with another tail size and one coarse
+    sweep each way is bit-identical to solo runs given the same tuning."""
+    tc = 256 if len(runs[0][0]) == 2 else 64
+    with chhs.Batch(runs) as b:
+        b.set_tuning(tc, 1, 1)
+        for q, r in enumerate(runs):
+            b.runs[q].set_phi(_phi0(r[0], q))
+        st, vb, _ = b.step(3)
+        assert all(s == chhs.CHHS_OK for s in st)
+        batched = [b.runs[q].get_state() for q in range(len(runs))]
+        with pytest.raises(chhs.ChhsError):
+            b.set_tuning(tc, 0, 0)  # no sweep at all: refused, the setting kept
+        st, _, _ = b.step(1)
+        assert all(s == chhs.CHHS_OK for s in st)
+    for q, (shape, h, eps, gamma, dt) in enumerate(runs):
+        with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=1)) as solo:
+            solo.set_tuning(tc, 8192, 512, 1, 1, 32, 16, 3)
+            solo.set_phi(_phi0(shape, q))
+            _, vs, _ = solo.step(3)
+            ref = solo.get_state()
+        assert vs == vb[q]
+        for a, c in zip(batched[q], ref):
+            assert np.array_equal(a, c), q
+
+
+def test_batch_autotune_keeps_every_state():
+    runs = RUNS_2D[:4]
+    with chhs.Batch(runs) as b:
+        for q, r in enumerate(runs):
+            b.runs[q].set_phi(_phi0(r[0], q))
+        b.step(2)
+        before = [b.runs[q].get_state() for q in range(len(runs))]
+        t = b.autotune(2)
+        assert t["tail_cells"] in (256, 1024, 4096) and (t["coarse_nu1"], t["coarse_nu2"]) in ((2, 2), (1, 1))
+        assert t["ms_per_step"] > 0
+        after = [b.runs[q].get_state() for q in range(len(runs))]
+        for x, y in zip(before, after):
+            for u, w in zip(x, y):
+                assert np.array_equal(u, w)
+        st, _, r = b.step(2)
+        assert all(s == chhs.CHHS_OK for s in st) and max(r) <= 1e-10

@@ -125,6 +125,8 @@ HANDLE_CALLS = {
     "chhs_batch_profile_step": (None, None, None),
     "chhs_set_tuning": (None, None),
     "chhs_norm_checks": (None, None),
+    "chhs_batch_set_tuning": (None, None),
+    "chhs_batch_autotune": (None, 1, None),
 }
 
 
