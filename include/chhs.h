@@ -229,6 +229,8 @@ typedef struct {
   int norm_f64_per8;  /* mixed form, double-single residual: of every 8 tiles of the residual
                          kernel, how many use double-precision instructions (0..8; default 3), so
                          that the FP64 pipe works beside the single-precision ones */
+  int coarse_tile_w, coarse_tile_h; /* 2D mixed form: tile interior on the levels below the finest */
+  int coarse_tile_threads;          /* (default 16 x 8 cells on 256 threads) and its block size */
   double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
                          the setting in force was timed (every candidate failed, or the fastest
                          could not be rebuilt and the original setting was kept) */
@@ -237,7 +239,8 @@ typedef struct {
 /* Autotuner of the handle's launch shapes and coarse sweep counts: tries
  * candidate settings (where the one-block tail starts; in double precision,
  * up to which level size the split update is used; in the 2D mixed form, the
- * tile block size and tile shape, 32 x 16, 32 x 32 or 64 x 16 cells; the
+ * tile block size and tile shape, 32 x 16, 32 x 32 or 64 x 16 cells, and on
+ * the levels below the finest the same shape or 16 x 8 cells on 256 threads; the
  * sweeps on the levels below the finest: the options' nu1, nu2 or, when both
  * exceed 1, one each), times
  * trial_steps steps of the handle's own problem from its current state with
@@ -257,7 +260,8 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out);
  * state is kept.  Errors: CHHS_ERR_INVALID_ARG (NULL, steps pending, a run
  * of a batch, tail_cells < 1, split_threads < 0, tile_threads not a multiple
  * of 32 in 32..1024, coarse sweep counts < 0 or both 0, tile sides odd or
- * below 2, tiles over 4096 cells, norm_f64_per8 outside 0..8, or a setting
+ * below 2, tiles over 4096 cells (the same for coarse_tile_*), norm_f64_per8
+ * outside 0..8, or a setting
  * the grid cannot take -- the
  * previous tuning is then kept), CHHS_ERR_CUDA. */
 chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* tuning);

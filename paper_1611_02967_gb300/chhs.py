@@ -61,7 +61,8 @@ class Tuning(ctypes.Structure):
     """chhs_tuning (include/chhs.h)."""
     _fields_ = [("tail_cells", ctypes.c_int), ("split_threads", ctypes.c_int), ("tile_threads", ctypes.c_int),
                 ("coarse_nu1", ctypes.c_int), ("coarse_nu2", ctypes.c_int), ("tile_w", ctypes.c_int),
-                ("tile_h", ctypes.c_int), ("norm_f64_per8", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("tile_h", ctypes.c_int), ("norm_f64_per8", ctypes.c_int), ("coarse_tile_w", ctypes.c_int),
+                ("coarse_tile_h", ctypes.c_int), ("coarse_tile_threads", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
 
 
 class ChhsError(RuntimeError):
@@ -338,13 +339,18 @@ class Run:
         self._check(lib().chhs_autotune(self.handle, int(trial_steps), ctypes.byref(t)))
         return dict(tail_cells=t.tail_cells, split_threads=t.split_threads, tile_threads=t.tile_threads,
                     coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2, tile_w=t.tile_w, tile_h=t.tile_h,
-                    norm_f64_per8=t.norm_f64_per8, ms_per_step=t.ms_per_step)
+                    norm_f64_per8=t.norm_f64_per8, coarse_tile=(t.coarse_tile_w, t.coarse_tile_h,
+                                                                 t.coarse_tile_threads),
+                    ms_per_step=t.ms_per_step)
 
     def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2, tile_w=32, tile_h=16,
-                   norm_f64_per8=3):
-        """chhs_set_tuning: apply launch shapes and coarse sweep counts."""
+                   norm_f64_per8=3, coarse_tile=(16, 8, 256)):
+        """chhs_set_tuning: apply launch shapes and coarse sweep counts
+        (coarse_tile: (width, height, threads) of the 2D mixed form's tiles
+        below the finest level)."""
+        cw, ch, ct = coarse_tile
         t = Tuning(int(tail_cells), int(split_threads), int(tile_threads), int(coarse_nu1), int(coarse_nu2),
-                   int(tile_w), int(tile_h), int(norm_f64_per8), 0.0)
+                   int(tile_w), int(tile_h), int(norm_f64_per8), int(cw), int(ch), int(ct), 0.0)
         self._check(lib().chhs_set_tuning(self.handle, ctypes.byref(t)))
 
     def mass(self):
@@ -522,7 +528,8 @@ class Batch:
     def set_tuning(self, tail_cells, coarse_nu1, coarse_nu2, norm_f64_per8=3):
         """chhs_batch_set_tuning: tail size, coarse sweep counts and the norm's
         FP64 share for every run; rebuilds the batch's graph."""
-        t = Tuning(int(tail_cells), 0, kTileThreads, int(coarse_nu1), int(coarse_nu2), 32, 16, int(norm_f64_per8), 0.0)
+        t = Tuning(int(tail_cells), 0, kTileThreads, int(coarse_nu1), int(coarse_nu2), 32, 16, int(norm_f64_per8),
+                   32, 16, kTileThreads, 0.0)
         self._check(lib().chhs_batch_set_tuning(self.handle, ctypes.byref(t)), "chhs_batch_set_tuning")
 
     def autotune(self, trial_steps=2):

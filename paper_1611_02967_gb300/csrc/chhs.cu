@@ -73,6 +73,12 @@ int level_fields(int dim, bool single) {
 // arithmetic, so that both kinds of pipes are busy (chhs_norm_df.cuh).
 constexpr int kNormF64Per8 = 3;
 
+// Tiles of the 2D single-precision levels below the finest (chhs_tuning's
+// coarse_tile_*): 16 x 8 cells on 256 threads measured 4% faster per 512^2
+// mixed-form step than the finest level's 32 x 16 on 512 (more blocks on the
+// levels of 256^2 and less; the finest level keeps its wider tiles).
+constexpr int kCoarseTileW = 16, kCoarseTileH = 8, kCoarseTileThreads = 256;
+
 // Levels with at most this many cells run inside the one-block tail kernel.
 // In double precision one SM does 2 FMA per clock and a single warp's
 // dependent FP64 chain is slow, so only the tiniest levels (8 x 8, 4 x 4 x 4)
@@ -192,7 +198,10 @@ struct chhs {
   int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kTileThreads;
   int norm_blocks = 1;              // grid of the stopping-norm kernels (whole blocks per SM)
   int nu1c = 2, nu2c = 2;           // sweeps on the levels below the finest (chhs_autotune; opts by default)
-  int tile_w = kTileW, tile_h = kTileH;  // tile interior of the 2D single-precision levels (chhs_autotune)
+  int tile_w = kTileW, tile_h = kTileH;  // tile interior of the 2D single-precision finest level (chhs_autotune)
+  // ... and of the levels below it, with its block size: smaller tiles there
+  // make more blocks on the small, latency-bound levels
+  int ctile_w = kCoarseTileW, ctile_h = kCoarseTileH, ctile_threads = kCoarseTileThreads;
   int norm_f64_per8 = kNormF64Per8;      // blocks of 8 whose residual runs on the FP64 pipe (mixed form)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
@@ -348,7 +357,8 @@ struct Enqueue {
     if constexpr (use_tiles<T>()) {
       // 2D single precision: pre-smoothing (+ right-hand side) + residual +
       // restriction in one tiled launch, prolongation + post-smoothing in another
-      const int tw = run->tile_w, th = run->tile_h;
+      const int tw = l == 0 ? run->tile_w : run->ctile_w, th = l == 0 ? run->tile_h : run->ctile_h;
+      const int tt = l == 0 ? run->tile_threads : run->ctile_threads;
       const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
       const int nf = tile_nfields<CORR>();
       const int np1 = 2 * nu_pre(run, l), np2 = 2 * nu_post(run, l);
@@ -372,12 +382,12 @@ struct Enqueue {
         to_state.p64 = run->lev[0].p;
       }
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_pre(run, l), [&] {
-        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, nf, sizeof(T), tw, th), s, L, C,
+        pdl_grid(k_tile<T, CORR>, grid, tt, tile_smem_bytes(np1 + 1, nf, sizeof(T), tw, th), s, L, C,
                  K, np1, np1 + 1, rhs ? 1 : 0, 0, 1, to_copy, (const int*)nullptr, tw, th);
       });
       vcycle<T, CORR>(run, s, lev, tail, l + 1);
       launch(run, s, l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH, (double)L.ncell * nu_post(run, l), [&] {
-        pdl_grid(k_tile<T, CORR>, grid, run->tile_threads, tile_smem_bytes(np2, nf, sizeof(T), tw, th), s, Lb, C, K,
+        pdl_grid(k_tile<T, CORR>, grid, tt, tile_smem_bytes(np2, nf, sizeof(T), tw, th), s, Lb, C, K,
                  np2, np2, 0, 1, 0, to_state, (const int*)nullptr, tw, th);
       });
       return;
@@ -505,7 +515,8 @@ struct Enqueue {
     CU(raise_to(ktail, smem));
     if constexpr (use_tiles<T>()) {
       const int halo = 2 * std::max(std::max(run->opts.nu1, run->opts.nu2), std::max(run->nu1c, run->nu2c)) + 1;
-      const size_t tb = tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->tile_w, run->tile_h);
+      const size_t tb = std::max(tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->tile_w, run->tile_h),
+                                 tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->ctile_w, run->ctile_h));
       const void* ktile = reinterpret_cast<const void*>(k_tile<T, CORR>);
       if (!fits(ktile, tb))
         return fail(run, CHHS_ERR_INVALID_ARG, "nu1/nu2 too large for the single-precision tiles");
@@ -928,6 +939,38 @@ chhs_status create_impl(int dim, const int n[3], double h, double eps, double ga
   return CHHS_OK;
 }
 
+// A handle's launch settings as a chhs_tuning, and back (ms_per_step unused).
+chhs_tuning current_tuning(const chhs_t* run) {
+  chhs_tuning t{};
+  t.tail_cells = run->tail_cells;
+  t.split_threads = run->split_threads;
+  t.tile_threads = run->tile_threads;
+  t.coarse_nu1 = run->nu1c;
+  t.coarse_nu2 = run->nu2c;
+  t.tile_w = run->tile_w;
+  t.tile_h = run->tile_h;
+  t.norm_f64_per8 = run->norm_f64_per8;
+  t.coarse_tile_w = run->ctile_w;
+  t.coarse_tile_h = run->ctile_h;
+  t.coarse_tile_threads = run->ctile_threads;
+  t.ms_per_step = -1.0;
+  return t;
+}
+
+void take_tuning(chhs_t* run, const chhs_tuning& t) {
+  run->tail_cells = t.tail_cells;
+  run->split_threads = t.split_threads;
+  run->tile_threads = t.tile_threads;
+  run->nu1c = t.coarse_nu1;
+  run->nu2c = t.coarse_nu2;
+  run->tile_w = t.tile_w;
+  run->tile_h = t.tile_h;
+  run->norm_f64_per8 = t.norm_f64_per8;
+  run->ctile_w = t.coarse_tile_w;
+  run->ctile_h = t.coarse_tile_h;
+  run->ctile_threads = t.coarse_tile_threads;
+}
+
 chhs_status copy_in(chhs_t* run, double* dst, const double* src, int on_device) {
   size_t bytes = sizeof(double) * run->ncell();
   CU(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -1230,37 +1273,32 @@ chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
   if (!run || !t) return fail(run, CHHS_ERR_INVALID_ARG, "NULL argument");
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
-  if (t->tail_cells < 1 || t->split_threads < 0 || t->tile_threads < 32 || t->tile_threads > 1024 ||
-      t->tile_threads % 32 != 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 || t->coarse_nu1 + t->coarse_nu2 < 1 ||
-      t->tile_w < 2 || t->tile_h < 2 || t->tile_w % 2 != 0 || t->tile_h % 2 != 0 || t->tile_w * t->tile_h > 4096 ||
-      t->norm_f64_per8 < 0 || t->norm_f64_per8 > 8)
+  auto tile_ok = [](int w, int h, int threads) {
+    return threads >= 32 && threads <= 1024 && threads % 32 == 0 && w >= 2 && h >= 2 && w % 2 == 0 && h % 2 == 0 &&
+           w * h <= 4096;
+  };
+  if (t->tail_cells < 1 || t->split_threads < 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 ||
+      t->coarse_nu1 + t->coarse_nu2 < 1 || !tile_ok(t->tile_w, t->tile_h, t->tile_threads) ||
+      !tile_ok(t->coarse_tile_w, t->coarse_tile_h, t->coarse_tile_threads) || t->norm_f64_per8 < 0 ||
+      t->norm_f64_per8 > 8)
     return fail(run, CHHS_ERR_INVALID_ARG, "invalid tuning");
   run->norm_f64_per8 = t->norm_f64_per8;
   run->err.clear();
   CU(cudaStreamSynchronize(run->stream));
-  const int keep[7] = {run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c, run->tile_w,
-                       run->tile_h};
-  auto rebuild = [&](int tc, int sp, int tt, int n1, int n2, int tw, int th) -> chhs_status {
+  const chhs_tuning keep = current_tuning(run);
+  auto rebuild = [&](const chhs_tuning& c) -> chhs_status {
     if (run->exec) cudaGraphExecDestroy(run->exec);
     if (run->graph) cudaGraphDestroy(run->graph);
     run->exec = nullptr;
     run->graph = nullptr;
-    run->tail_cells = tc;
-    run->split_threads = sp;
-    run->tile_threads = tt;
-    run->nu1c = n1;
-    run->nu2c = n2;
-    run->tile_w = tw;
-    run->tile_h = th;
+    take_tuning(run, c);
     place_tail(run);
     return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
   };
-  chhs_status s = rebuild(t->tail_cells, t->split_threads, t->tile_threads, t->coarse_nu1, t->coarse_nu2, t->tile_w,
-                          t->tile_h);
+  chhs_status s = rebuild(*t);
   if (s != CHHS_OK) {
     const std::string why = run->err;
-    if (rebuild(keep[0], keep[1], keep[2], keep[3], keep[4], keep[5], keep[6]) != CHHS_OK)
-      return fail(run, CHHS_ERR_CUDA, "could not rebuild the step graph");
+    if (rebuild(keep) != CHHS_OK) return fail(run, CHHS_ERR_CUDA, "could not rebuild the step graph");
     return fail(run, s, why.empty() ? "tuning refused" : why);
   }
   return CHHS_OK;
@@ -1271,10 +1309,23 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   if (run->batch_member) return fail(run, CHHS_ERR_INVALID_ARG, "a run of a batch takes the batch's launch shapes");
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");
   run->err.clear();
-  struct Cand {
-    int tail_cells, split_threads, tile_threads, nu1c, nu2c, tile_w, tile_h;
-  };
+  using Cand = chhs_tuning;
   std::vector<Cand> cands;
+  const chhs_tuning base = current_tuning(run);
+  auto cand = [&](int tc, int sp, int tt, int n1, int n2, int tw, int th, int ctw, int cth, int ctt) {
+    chhs_tuning c = base;
+    c.tail_cells = tc;
+    c.split_threads = sp;
+    c.tile_threads = tt;
+    c.coarse_nu1 = n1;
+    c.coarse_nu2 = n2;
+    c.tile_w = tw;
+    c.tile_h = th;
+    c.coarse_tile_w = ctw;
+    c.coarse_tile_h = cth;
+    c.coarse_tile_threads = ctt;
+    cands.push_back(c);
+  };
   const bool mixed = run->opts.precision == 1;
   // sweep counts below the finest level: the options' own, and one sweep
   // each way when the options ask for more (fewer passes on the small,
@@ -1287,18 +1338,24 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     int tt, tw, th;
   };
   const Shape2 shapes[4] = {{256, 32, 16}, {512, 32, 16}, {512, 32, 32}, {512, 64, 16}};
+  // the levels below the finest: the finest level's shape, or the small one
+  const Shape2 small{kCoarseTileThreads, kCoarseTileW, kCoarseTileH};
   for (const auto& cn : coarse) {
     if (!mixed) {
       const int tails[2] = {64, run->dim == 2 ? 256 : 512};
       for (int tc : tails)
         for (int sp : {0, 8192, 32768})
-          cands.push_back({tc, sp, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h});
+          cand(tc, sp, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h, run->ctile_w, run->ctile_h,
+               run->ctile_threads);
     } else if (run->dim == 2) {
       for (int tc : {256, 1024, 2048})
-        for (const Shape2& sh : shapes) cands.push_back({tc, run->split_threads, sh.tt, cn.first, cn.second, sh.tw, sh.th});
+        for (const Shape2& sh : shapes)
+          for (const Shape2& cs : {sh, small})
+            cand(tc, run->split_threads, sh.tt, cn.first, cn.second, sh.tw, sh.th, cs.tw, cs.th, cs.tt);
     } else {
       for (int tc : {64, 512})
-        cands.push_back({tc, run->split_threads, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h});
+        cand(tc, run->split_threads, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h, run->ctile_w,
+             run->ctile_h, run->ctile_threads);
     }
   }
   // the run's state (phi^m, phi^{m-1}, mu, p), restored before every trial and at the end
@@ -1336,18 +1393,11 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     if (run->graph) cudaGraphDestroy(run->graph);
     run->exec = nullptr;
     run->graph = nullptr;
-    run->tail_cells = c.tail_cells;
-    run->split_threads = c.split_threads;
-    run->tile_threads = c.tile_threads;
-    run->nu1c = c.nu1c;
-    run->nu2c = c.nu2c;
-    run->tile_w = c.tile_w;
-    run->tile_h = c.tile_h;
+    take_tuning(run, c);
     place_tail(run);
     return run->dim == 2 ? Enqueue<2>::build_graph(run) : Enqueue<3>::build_graph(run);
   };
-  const Cand orig{run->tail_cells, run->split_threads, run->tile_threads, run->nu1c, run->nu2c, run->tile_w,
-                  run->tile_h};
+  const Cand orig = base;
   Cand best = orig;
   float best_ms = -1.f;
   chhs_status s;
@@ -1377,14 +1427,7 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
   if ((s = restore()) != CHHS_OK) return s;
   CU(cudaStreamSynchronize(run->stream));
   if (out) {
-    out->tail_cells = run->tail_cells;
-    out->split_threads = run->split_threads;
-    out->tile_threads = run->tile_threads;
-    out->coarse_nu1 = run->nu1c;
-    out->coarse_nu2 = run->nu2c;
-    out->tile_w = run->tile_w;
-    out->tile_h = run->tile_h;
-    out->norm_f64_per8 = run->norm_f64_per8;
+    *out = current_tuning(run);
     out->ms_per_step = best_ms < 0.f ? -1.0 : (double)best_ms / trial_steps;
   }
   return CHHS_OK;
@@ -2359,6 +2402,9 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
     out->tile_w = kTileW;
     out->tile_h = kTileH;
     out->norm_f64_per8 = r->norm_f64_per8;
+    out->coarse_tile_w = kTileW;
+    out->coarse_tile_h = kTileH;
+    out->coarse_tile_threads = kTileThreads;
     out->ms_per_step = best_ms < 0.f ? -1.0 : best_ms / trial_steps;
   }
   return CHHS_OK;
