@@ -182,7 +182,8 @@ enum {
  * kernels one by one (no graph) with a CUDA event pair around each, and add
  * into the caller's arrays of CHHS_K_COUNT entries: device milliseconds,
  * launches and work units per kernel kind.  For profiling only: the host
- * reads the stopping norm after every V-cycle.  CHHS_ERR_INVALID_ARG while
+ * reads the loop decision after every stopping norm and launches the
+ * V-cycles it asks for.  CHHS_ERR_INVALID_ARG while
  * steps of chhs_step_async are pending (call chhs_wait first). */
 chhs_status chhs_profile_step(chhs_t* run, double* ms_out, long long* launches_out, double* units_out);
 

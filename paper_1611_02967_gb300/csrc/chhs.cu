@@ -6,11 +6,13 @@
 //   restrict phi^m, phi* to every coarse level
 //   stopping norm -> while-loop condition
 //   WHILE (norm > tol and V < max_v):                 Section 5 preamble
-//       V(nu1, nu2)-cycle; stopping norm -> condition
+//       IF (inner >= 3) V-cycle; IF (inner >= 2) V-cycle;
+//       V(nu1, nu2)-cycle; stopping norm -> conditions
 //   mean of p; accept the step (rotate phi^m, phi^{m-1})
 // The loop is a conditional graph node whose condition a device kernel sets,
-// so a step needs no host round trip; chhs_step(n) launches the graph n times
-// and reads the device status once.
+// so a step needs no host round trip; the norm kernel also predicts how many
+// V-cycles the next iteration runs (loop_decision).  chhs_step(n) launches
+// the graph n times and reads the device status once.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -3,7 +3,7 @@
 // significant bits, computed on the single-precision pipes.
 //
 // GB300 runs double precision at 1/64 of the single-precision rate, and the
-// mixed-precision form's one double-precision kernel per V-cycle -- the
+// mixed-precision form's one double-precision kernel per iteration -- the
 // defect-correction residual f - N(u) -- was bound by that pipe.  The
 // residual only has to be accurate to far below the stopping tolerance
 // (1e-10 against values of order one), which 48 bits give.  The operations
