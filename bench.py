@@ -146,9 +146,13 @@ def kernel_hash():
 
 
 def file_hash(path):
-    """Hash of a kernel source file (a recorded traffic figure holds while it matches)."""
+    """Hash of a kernel source file up to its restriction section (the 3D
+    colour pass and what it calls; a recorded traffic figure holds while it
+    matches)."""
     with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        src = f.read()
+    cut = src.find(b"// ---------------------------------------------------------------- restriction")
+    return hashlib.sha256(src[:cut if cut > 0 else len(src)]).hexdigest()[:16]
 
 
 def measured_traffic(path=None, src=None):

@@ -445,9 +445,8 @@ struct Enqueue {
         launch(run, s, kind, colour_cells(L, colour), [&] {
           pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, (rhs && it == 0) ? 1 : 0, 0, none);
         });
-    constexpr int TX = DIM == 3 ? 8 : 16;
-    const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
-    const int rblocks = (int)((tiles * 32 + kBlock - 1) / kBlock);
+    const long long warps = rr_c_warps(DIM, L.nx, L.ny, L.nz);
+    const int rblocks = (int)((warps * 32 + kBlock - 1) / kBlock);
     launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
       pdl(k_residual_restrict_c<DIM>, rblocks, kBlock, s, L, C, K);
     });
@@ -1829,9 +1828,8 @@ struct BatchStep {
       }
     JobList<PairJob> jr;
     runs_at([&](chhs_t* r, const Level<float>& L, const Level<float>& C) {
-      constexpr int TX = DIM == 3 ? 8 : 16;
-      const long long tiles = (long long)((L.nx + TX - 1) / TX) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
-      jr.add(PairJob{L, C, k32(r), Level<double>{}, gate(r)}, (int)((tiles * 32 + kBlock - 1) / kBlock));
+      const long long warps = rr_c_warps(DIM, L.nx, L.ny, L.nz);
+      jr.add(PairJob{L, C, k32(r), Level<double>{}, gate(r)}, (int)((warps * 32 + kBlock - 1) / kBlock));
     });
     go(CHHS_K_RESTRICT, jr, kb_residual_restrict_c<DIM>, kBlock, 0, s);
   }

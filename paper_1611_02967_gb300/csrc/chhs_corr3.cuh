@@ -213,56 +213,127 @@ __global__ void __launch_bounds__(kSmoothBlock, 8) k_smooth_c(const __grid_const
   smooth_c_body<DIM>(blockIdx.x, L, C, K, colour, rhs, pro, U);
 }
 
-// Residual of the correction form and its restriction (k_residual_restrict's
-// warp tiles of 16 x 2 / 8 x 2 x 2 fine cells, children summed by shuffles),
-// with recomputed coefficients.  Writes u_c = u_c^0 = R e, f_c = R r and
-// phi_b,c = R phi_b.
+// ---------------------------------------------------------------- restriction
+
+// Face data of a cell from its phi* value pc and its neighbours' pe[] (the
+// cell's own value where in[q] is false), as faces_c forms it from indices.
+template <int DIM>
+__device__ __forceinline__ void faces_vals(const Coefs<float>& K, float pc, const float (&pe)[6], const bool (&in)[6],
+                                           FacesC<DIM>& F) {
+  F.sM = -0.f;
+  F.sa = -0.f;
+  F.m = 0;
+  F.in = 0u;
+#pragma unroll
+  for (int q = 0; q < 2 * DIM; ++q) {
+    const float af = 0.5f * (pc + pe[q]);
+    F.e[q] = 0;
+    F.a[q] = in[q] ? af : 0.f;
+    F.M[q] = in[q] ? 1.f + K.gamma * af * af : 0.f;
+    F.sM += F.M[q];
+    F.sa += F.a[q];
+    F.m += in[q] ? 1 : 0;
+    F.in |= in[q] ? (1u << q) : 0u;
+  }
+}
+
+// Warps of k_residual_restrict_c on an nx x ny (x nz) level: each covers 2 *
+// rr_c_pairs(dim) x 2 (x 2) fine cells, a lane an x-pair of them.
+__host__ __device__ constexpr int rr_c_pairs(int dim) { return dim == 3 ? 8 : 16; }
+__host__ __device__ inline long long rr_c_warps(int dim, int nx, int ny, int nz) {
+  const int px = rr_c_pairs(dim);
+  return (long long)((nx + 2 * px - 1) / (2 * px)) * (ny / 2) * (dim == 3 ? nz / 2 : 1);
+}
+
+// Residual of the correction form and its restriction, with recomputed
+// coefficients.  A lane takes the x-pair (i, i+1), i even -- two children of
+// one coarse cell -- and reads every field as float2 pairs (the pair, and
+// the pairs beside it in y and z; the two x neighbours outside the pair as
+// single values), so a warp's loads are 8-byte vector loads over 2 * 8 x 2 x
+// 2 (3D) or 2 * 16 x 2 (2D) fine cells.  The pair's two residuals are added
+// in the lane, then the other children by shuffles in y and z (the order of
+// the additions of one lane per cell and shuffles over x, y, z).  Writes
+// u_c = u_c^0 = R e, f_c = R r and phi_b,c = R phi_b.
 template <int DIM>
 __device__ __forceinline__ void residual_restrict_c_body(int bx, const Level<float>& F, const Level<float>& C,
                                                          const Coefs<float>& K) {
-  constexpr int TX = DIM == 3 ? 8 : 16;
+  constexpr int PX = rr_c_pairs(DIM);
   const int lane = threadIdx.x & 31;
   const int warp = (bx * blockDim.x + threadIdx.x) >> 5;
-  const int tiles_x = (F.nx + TX - 1) / TX;
+  const int tiles_x = (F.nx + 2 * PX - 1) / (2 * PX);
   const int tiles_y = F.ny >> 1;
   const int tiles_z = DIM == 3 ? (F.nz >> 1) : 1;
   if (warp >= tiles_x * tiles_y * tiles_z) return;  // whole warp
   const int tx = warp % tiles_x;
   const int rest = warp / tiles_x;
   const int ty = rest % tiles_y, tz = rest / tiles_y;
-  const int i = tx * TX + (lane % TX);
-  const int j = 2 * ty + ((lane / TX) & 1);
+  const int i = tx * 2 * PX + 2 * (lane % PX);  // the pair (i, i + 1); nx is even
+  const int j = 2 * ty + ((lane / PX) & 1);
   const int k = DIM == 3 ? 2 * tz + (lane >> 4) : 0;
   const bool valid = i < F.nx;
   float v[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) v[q] = 0.f;
   if (valid) {
-    const int c = i + F.nx * (j + F.ny * k);
-    FacesC<DIM> Fc;
-    faces_c<DIM>(F, K, c, i, j, k, Fc);
-    const Val3 u{F.phi[c], F.mu[c], F.p[c]};
-    Val3 nb[2 * DIM];
+    const int c = i + F.nx * (j + F.ny * k);  // even
+    const int sy = F.nx, sz = F.nx * F.ny;
+    const bool xm = i > 0, xp = i + 2 < F.nx, ym = j > 0, yp = j + 1 < F.ny;
+    const bool zm = DIM == 3 && k > 0, zp = DIM == 3 && k + 1 < F.nz;
+    auto ld2 = [](const float* a, int x) { return *reinterpret_cast<const float2*>(a + x); };
+    // the pair and its y/z neighbour pairs (the pair itself on a missing face)
+    auto pairs = [&](const float* a, float2 (&P)[5]) {
+      P[0] = ld2(a, c);
+      P[1] = ym ? ld2(a, c - sy) : P[0];
+      P[2] = yp ? ld2(a, c + sy) : P[0];
+      P[3] = zm ? ld2(a, c - sz) : P[0];
+      P[4] = zp ? ld2(a, c + sz) : P[0];
+    };
+    float2 S[5], Ph[5], Mu[5], Pr[5];
+    pairs(F.phis, S);
+    pairs(F.phi, Ph);
+    pairs(F.mu, Mu);
+    pairs(F.p, Pr);
+    const float sxm = xm ? F.phis[c - 1] : S[0].x, sxp = xp ? F.phis[c + 2] : S[0].y;
+    const Val3 uxm = xm ? Val3{F.phi[c - 1], F.mu[c - 1], F.p[c - 1]} : Val3{Ph[0].x, Mu[0].x, Pr[0].x};
+    const Val3 uxp = xp ? Val3{F.phi[c + 2], F.mu[c + 2], F.p[c + 2]} : Val3{Ph[0].y, Mu[0].y, Pr[0].y};
+    const float2 f1 = ld2(F.fphi, c), f2 = ld2(F.fmu, c), f3 = ld2(F.fp, c), pm = ld2(F.phim, c),
+                 pb = ld2(F.phib, c);
+    const bool yzin[4] = {ym, yp, zm, zp};
 #pragma unroll
-    for (int q = 0; q < 2 * DIM; ++q) nb[q] = Val3{F.phi[Fc.e[q]], F.mu[Fc.e[q]], F.p[Fc.e[q]]};
-    const float phib = F.phib[c];
-    float n1, n2, n3;
-    n_corr<DIM>(F, K, Fc, u, nb, phib, F.phim[c], n1, n2, n3);
-    v[0] = F.fphi[c] - n1;
-    v[1] = F.fmu[c] - n2;
-    v[2] = F.fp[c] - n3;
-    v[3] = u.phi;
-    v[4] = u.mu;
-    v[5] = u.p;
-    v[6] = phib;
+    for (int h = 0; h < 2; ++h) {  // the pair's cells, i then i + 1
+      auto cx = [h](const float2& a) { return h ? a.y : a.x; };
+      const bool in[6] = {h ? true : xm, h ? xp : true, yzin[0], yzin[1], yzin[2], yzin[3]};
+      const Val3 u{cx(Ph[0]), cx(Mu[0]), cx(Pr[0])};
+      const Val3 other{h ? Ph[0].x : Ph[0].y, h ? Mu[0].x : Mu[0].y, h ? Pr[0].x : Pr[0].y};
+      const float pc = cx(S[0]);
+      float pe[6];
+      Val3 nb[2 * DIM];
+      pe[0] = h ? S[0].x : sxm;
+      pe[1] = h ? sxp : S[0].y;
+      nb[0] = h ? other : uxm;
+      nb[1] = h ? uxp : other;
+#pragma unroll
+      for (int q = 2; q < 2 * DIM; ++q) {
+        pe[q] = cx(S[q - 1]);
+        nb[q] = Val3{cx(Ph[q - 1]), cx(Mu[q - 1]), cx(Pr[q - 1])};
+      }
+      if (DIM == 2) pe[4] = pe[5] = pc;
+      FacesC<DIM> Fc;
+      faces_vals<DIM>(K, pc, pe, in, Fc);
+      const float phib = cx(pb);
+      float n1, n2, n3;
+      n_corr<DIM>(F, K, Fc, u, nb, phib, cx(pm), n1, n2, n3);
+      const float r[7] = {cx(f1) - n1, cx(f2) - n2, cx(f3) - n3, u.phi, u.mu, u.p, phib};
+#pragma unroll
+      for (int q = 0; q < 7; ++q) v[q] = h ? v[q] + r[q] : r[q];
+    }
   }
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
-    v[q] += __shfl_xor_sync(0xffffffffu, v[q], TX);
+    v[q] += __shfl_xor_sync(0xffffffffu, v[q], PX);
     if (DIM == 3) v[q] += __shfl_xor_sync(0xffffffffu, v[q], 16);
   }
-  const bool leader = valid && (lane & 1) == 0 && ((lane / TX) & 1) == 0 && (DIM == 2 || lane < 16);
+  const bool leader = valid && ((lane / PX) & 1) == 0 && (DIM == 2 || lane < 16);
   if (!leader) return;
   const float w = DIM == 3 ? 0.125f : 0.25f;
   const int q = (i >> 1) + C.nx * ((j >> 1) + C.ny * (k >> 1));
