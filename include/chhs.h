@@ -453,18 +453,22 @@ chhs_status chhs_batch_step(chhs_batch_t* batch, int nsteps, int* status_out, in
 /* Apply launch settings to every run of the batch and rebuild its step
  * graph; the runs' states are kept.  Of chhs_tuning the batch takes
  * tail_cells, coarse_nu1, coarse_nu2 and norm_f64_per8 (the same for all its
- * runs; its tiles keep 32 x 16 cells of 512 threads and the other fields are
- * ignored).  Errors: CHHS_ERR_INVALID_ARG (NULL, tail_cells < 1, coarse
- * sweep counts < 0 or both 0, norm_f64_per8 outside 0..8, or a setting some
- * run cannot take -- the previous setting is then kept), CHHS_ERR_CUDA.  The
- * paper has no counterpart. */
+ * runs) and, in 2D, tile_w, tile_h and tile_threads for the per-run tile
+ * launches of its large levels (default 32 x 32 cells on 512 threads; the
+ * batched launch of the small levels keeps 32 x 16 on 512); the other fields
+ * are ignored.  Errors:
+ * CHHS_ERR_INVALID_ARG (NULL, tail_cells < 1, coarse sweep counts < 0 or both
+ * 0, norm_f64_per8 outside 0..8, a tile as chhs_set_tuning refuses, or a
+ * setting some run cannot take -- the previous setting is then kept),
+ * CHHS_ERR_CUDA.  The paper has no counterpart. */
 chhs_status chhs_batch_set_tuning(chhs_batch_t* batch, const chhs_tuning* tuning);
 
 /* Autotuner of the batch: times trial_steps steps of all its runs from
  * their current states with each candidate setting (where the one-block
  * tail starts: levels of at most 256 / 1024 / 4096 cells in 2D, 64 / 512 /
  * 4096 in 3D; the sweeps below the finest level: the options' nu1, nu2 or,
- * when both exceed 1, one each), keeps the fastest and rebuilds the batch's
+ * when both exceed 1, one each; in 2D the large levels' tile shape, 32 x 16,
+ * 32 x 32 or 64 x 16 cells), keeps the fastest and rebuilds the batch's
  * graph with it.  Every run's state is restored after each trial and at the
  * end.  Candidates that fail are skipped.  Allocates a temporary copy of
  * all states (4 doubles per cell).  out (nullable) receives the setting

@@ -525,10 +525,12 @@ class Batch:
         if st != CHHS_OK:
             raise ChhsError(st, "%s: %s" % (what, lib().chhs_batch_last_error(self.handle).decode()))
 
-    def set_tuning(self, tail_cells, coarse_nu1, coarse_nu2, norm_f64_per8=3):
+    def set_tuning(self, tail_cells, coarse_nu1, coarse_nu2, norm_f64_per8=3, tile=(32, 16, 512)):
         """chhs_batch_set_tuning: tail size, coarse sweep counts and the norm's
-        FP64 share for every run; rebuilds the batch's graph."""
-        t = Tuning(int(tail_cells), 0, kTileThreads, int(coarse_nu1), int(coarse_nu2), 32, 16, int(norm_f64_per8),
+        FP64 share for every run, and (width, height, threads) of the per-run
+        tile launches of large 2D levels; rebuilds the batch's graph."""
+        tw, th, tt = tile
+        t = Tuning(int(tail_cells), 0, int(tt), int(coarse_nu1), int(coarse_nu2), int(tw), int(th), int(norm_f64_per8),
                    32, 16, kTileThreads, 0.0)
         self._check(lib().chhs_batch_set_tuning(self.handle, ctypes.byref(t)), "chhs_batch_set_tuning")
 
@@ -538,7 +540,8 @@ class Batch:
         t = Tuning()
         self._check(lib().chhs_batch_autotune(self.handle, int(trial_steps), ctypes.byref(t)), "chhs_batch_autotune")
         return dict(tail_cells=t.tail_cells, coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2,
-                    norm_f64_per8=t.norm_f64_per8, ms_per_step=t.ms_per_step)
+                    norm_f64_per8=t.norm_f64_per8, tile=(t.tile_w, t.tile_h, t.tile_threads),
+                    ms_per_step=t.ms_per_step)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1566,6 +1566,10 @@ struct chhs_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches_per_v = 0, launches_per_step = 0;
+  // tile shape of the per-run tile launches of large 2D levels (the batched
+  // launch of the small levels keeps 32 x 16 on 512 threads); 32 x 32 took
+  // the batched configuration from 6.3e8 to 7.2e8 cell-steps/s
+  int big_tw = 32, big_th = 32, big_tt = kTileThreads;
   std::string err;
 };
 
@@ -1615,7 +1619,7 @@ struct BatchStep {
   std::vector<size_t> offs;         // table offsets in emission order
   size_t cur = 0;
   int* counter = nullptr;           // launches, while capturing
-  size_t tile_smem = 0, tail_smem = 0;
+  size_t tile_smem = 0, tile_smem_big = 0, tail_smem = 0;
 
   size_t put(const void* p, size_t n) {
     const size_t off = align_up(buf.size());
@@ -1751,10 +1755,11 @@ struct BatchStep {
   void go_tile(int kind, const TileJob<float>& J, int blocks, cudaStream_t s) {
     if (!capture) return;
     if (counter) ++*counter;
-    const dim3 grid((unsigned)J.gx, (unsigned)(blocks / J.gx));
+    const int tw = b->big_tw, th = b->big_th;
+    const dim3 grid((unsigned)((J.L.nx + tw - 1) / tw), (unsigned)((J.L.ny + th - 1) / th));
     timed(kind, [&] {
-      pdl_grid(k_tile<float, true>, grid, kTileThreads, tile_smem, s, J.L, J.C, J.K, J.npass, J.halo, J.rhs,
-               J.prolong, J.restrict_out, J.out, J.gate, (int)kTileW, (int)kTileH);
+      pdl_grid(k_tile<float, true>, grid, b->big_tt, tile_smem_big, s, J.L, J.C, J.K, J.npass, J.halo, J.rhs,
+               J.prolong, J.restrict_out, J.out, J.gate, tw, th);
     }, s);
   }
   // Side streams of the capture: the big per-run tile launches of one phase
@@ -1919,6 +1924,7 @@ struct BatchStep {
     if (DIM == 2) {
       const int halo = 2 * std::max(std::max(b->opts.nu1, b->opts.nu2), std::max(b->runs[0]->nu1c, b->runs[0]->nu2c)) + 1;
       tile_smem = tile_smem_bytes(halo, tile_nfields<true>(), sizeof(float));
+      tile_smem_big = tile_smem_bytes(halo, tile_nfields<true>(), sizeof(float), b->big_tw, b->big_th);
     }
     auto raise_to = [&](const void* fn, size_t dyn) -> chhs_status {
       cudaFuncAttributes fa;
@@ -1934,7 +1940,7 @@ struct BatchStep {
     if (DIM == 2) {
       st = raise_to(reinterpret_cast<const void*>(kb_tile<float, true>), tile_smem);
       if (st != CHHS_OK) return st;
-      st = raise_to(reinterpret_cast<const void*>(k_tile<float, true>), tile_smem);
+      st = raise_to(reinterpret_cast<const void*>(k_tile<float, true>), std::max(tile_smem, tile_smem_big));
       if (st != CHHS_OK) return st;
     }
     return CHHS_OK;
@@ -2266,8 +2272,12 @@ chhs_status chhs_batch_launch_counts(const chhs_batch_t* b, int* per_vcycle, int
 namespace {
 
 // Apply a tuning to every run of the batch and rebuild its step graph.
-chhs_status batch_apply(chhs_batch_t* b, int tail_cells, int nu1c, int nu2c, int norm_f64_per8) {
+chhs_status batch_apply(chhs_batch_t* b, int tail_cells, int nu1c, int nu2c, int norm_f64_per8, int tw, int th,
+                        int tt) {
   BCU(cudaStreamSynchronize(b->stream));
+  b->big_tw = tw;
+  b->big_th = th;
+  b->big_tt = tt;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->tables) cudaFree(b->tables);
@@ -2296,7 +2306,9 @@ chhs_status batch_apply(chhs_batch_t* b, int tail_cells, int nu1c, int nu2c, int
 
 bool batch_tuning_ok(const chhs_tuning* t) {
   return t && t->tail_cells >= 1 && t->coarse_nu1 >= 0 && t->coarse_nu2 >= 0 &&
-         t->coarse_nu1 + t->coarse_nu2 >= 1 && t->norm_f64_per8 >= 0 && t->norm_f64_per8 <= 8;
+         t->coarse_nu1 + t->coarse_nu2 >= 1 && t->norm_f64_per8 >= 0 && t->norm_f64_per8 <= 8 &&
+         t->tile_threads >= 32 && t->tile_threads <= 1024 && t->tile_threads % 32 == 0 && t->tile_w >= 2 &&
+         t->tile_h >= 2 && t->tile_w % 2 == 0 && t->tile_h % 2 == 0 && t->tile_w * t->tile_h <= 4096;
 }
 
 }  // namespace
@@ -2308,11 +2320,13 @@ chhs_status chhs_batch_set_tuning(chhs_batch_t* b, const chhs_tuning* t) {
   if (!batch_tuning_ok(t)) return bfail(b, CHHS_ERR_INVALID_ARG, "invalid tuning");
   b->err.clear();
   const chhs_t* r0 = b->runs[0];
-  const int keep[4] = {r0->tail_cells, r0->nu1c, r0->nu2c, r0->norm_f64_per8};
-  chhs_status s = batch_apply(b, t->tail_cells, t->coarse_nu1, t->coarse_nu2, t->norm_f64_per8);
+  const int keep[7] = {r0->tail_cells, r0->nu1c, r0->nu2c, r0->norm_f64_per8, b->big_tw, b->big_th, b->big_tt};
+  chhs_status s = batch_apply(b, t->tail_cells, t->coarse_nu1, t->coarse_nu2, t->norm_f64_per8, t->tile_w, t->tile_h,
+                              t->tile_threads);
   if (s == CHHS_OK) return CHHS_OK;
   const std::string why = b->err;
-  if (batch_apply(b, keep[0], keep[1], keep[2], keep[3]) != CHHS_OK) return bfail(b, CHHS_ERR_CUDA, why);
+  if (batch_apply(b, keep[0], keep[1], keep[2], keep[3], keep[4], keep[5], keep[6]) != CHHS_OK)
+    return bfail(b, CHHS_ERR_CUDA, why);
   return bfail(b, s == CHHS_ERR_CUDA ? CHHS_ERR_CUDA : CHHS_ERR_INVALID_ARG, why);
 }
 
@@ -2343,15 +2357,20 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
     return cudaStreamSynchronize(b->stream) == cudaSuccess;
   };
   struct Cand {
-    int tc, n1, n2;
+    int tc, n1, n2, tw, th, tt;
   };
   const chhs_t* r0 = b->runs[0];
-  const Cand orig{r0->tail_cells, r0->nu1c, r0->nu2c};
+  const Cand orig{r0->tail_cells, r0->nu1c, r0->nu2c, b->big_tw, b->big_th, b->big_tt};
   std::vector<Cand> cands;
   std::vector<std::pair<int, int>> coarse = {{b->opts.nu1, b->opts.nu2}};
   if (b->opts.nu1 > 1 && b->opts.nu2 > 1) coarse.push_back({1, 1});
+  // 2D: the tile shape of the per-run launches of large levels as well
+  const int shapes2[3][3] = {{kTileW, kTileH, kTileThreads}, {32, 32, 512}, {64, 16, 512}};
+  const int nshapes = b->dim == 2 ? 3 : 1;
   for (const auto& cn : coarse)
-    for (int tc : {b->dim == 2 ? 256 : 64, b->dim == 2 ? 1024 : 512, 4096}) cands.push_back({tc, cn.first, cn.second});
+    for (int tc : {b->dim == 2 ? 256 : 64, b->dim == 2 ? 1024 : 512, 4096})
+      for (int q = 0; q < nshapes; ++q)
+        cands.push_back({tc, cn.first, cn.second, shapes2[q][0], shapes2[q][1], shapes2[q][2]});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   chhs_status s = CHHS_OK;
   float best_ms = -1.f;
@@ -2360,7 +2379,7 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
     s = CHHS_ERR_CUDA;
   for (size_t q = 0; s == CHHS_OK && q < cands.size(); ++q) {
     const Cand& c = cands[q];
-    if (batch_apply(b, c.tc, c.n1, c.n2, r0->norm_f64_per8) != CHHS_OK) continue;  // e.g. a tail too big
+    if (batch_apply(b, c.tc, c.n1, c.n2, r0->norm_f64_per8, c.tw, c.th, c.tt) != CHHS_OK) continue;  // e.g. a tail too big
     // one untimed step (the new graph's first launch), then the timed ones,
     // each from the saved state
     bool ok = copy_states(false) && chhs_batch_step(b, 1, nullptr, nullptr, nullptr) == CHHS_OK && copy_states(false);
@@ -2381,9 +2400,10 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
       best = c;
     }
   }
-  if (s == CHHS_OK && batch_apply(b, best.tc, best.n1, best.n2, r0->norm_f64_per8) != CHHS_OK) {
+  if (s == CHHS_OK && batch_apply(b, best.tc, best.n1, best.n2, r0->norm_f64_per8, best.tw, best.th, best.tt) != CHHS_OK) {
     best_ms = -1.f;  // the fastest could not be rebuilt: back to the original setting
-    if (batch_apply(b, orig.tc, orig.n1, orig.n2, r0->norm_f64_per8) != CHHS_OK) s = CHHS_ERR_CUDA;
+    if (batch_apply(b, orig.tc, orig.n1, orig.n2, r0->norm_f64_per8, orig.tw, orig.th, orig.tt) != CHHS_OK)
+      s = CHHS_ERR_CUDA;
   }
   if (s == CHHS_OK && !copy_states(false)) s = CHHS_ERR_CUDA;
   if (e0) cudaEventDestroy(e0);
@@ -2396,11 +2416,11 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
     const chhs_t* r = b->runs[0];
     out->tail_cells = r->tail_cells;
     out->split_threads = r->split_threads;
-    out->tile_threads = kTileThreads;
+    out->tile_threads = b->big_tt;
     out->coarse_nu1 = r->nu1c;
     out->coarse_nu2 = r->nu2c;
-    out->tile_w = kTileW;
-    out->tile_h = kTileH;
+    out->tile_w = b->big_tw;
+    out->tile_h = b->big_th;
     out->norm_f64_per8 = r->norm_f64_per8;
     out->coarse_tile_w = kTileW;
     out->coarse_tile_h = kTileH;

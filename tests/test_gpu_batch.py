@@ -153,7 +153,7 @@ def test_batch_tuning_matches_solo_runs_with_the_same_tuning(runs):
     sweep each way is bit-identical to solo runs given the same tuning."""
     tc = 256 if len(runs[0][0]) == 2 else 64
     with chhs.Batch(runs) as b:
-        b.set_tuning(tc, 1, 1)
+        b.set_tuning(tc, 1, 1, tile=(32, 32, 512))  # the large levels' tiles: no effect on results
         for q, r in enumerate(runs):
             b.runs[q].set_phi(_phi0(r[0], q))
         st, vb, _ = b.step(3)
@@ -183,6 +183,7 @@ def test_batch_autotune_keeps_every_state():
         before = [b.runs[q].get_state() for q in range(len(runs))]
         t = b.autotune(2)
         assert t["tail_cells"] in (256, 1024, 4096) and (t["coarse_nu1"], t["coarse_nu2"]) in ((2, 2), (1, 1))
+        assert t["tile"] in ((32, 16, 512), (32, 32, 512), (64, 16, 512))
         assert t["ms_per_step"] > 0
         after = [b.runs[q].get_state() for q in range(len(runs))]
         for x, y in zip(before, after):
@@ -190,3 +191,26 @@ def test_batch_autotune_keeps_every_state():
                 assert np.array_equal(u, w)
         st, _, r = b.step(2)
         assert all(s == chhs.CHHS_OK for s in st) and max(r) <= 1e-10
+
+
+@pytest.mark.parametrize("tile", [(32, 16, 512), (32, 32, 512), (64, 16, 512)])
+def test_batch_large_level_tile_shapes_match_solo_runs(tile):
+    """A 512^2 run's finest level goes to its own tile launch inside the
+    batch (with the tile shape of chhs_batch_set_tuning), the 64^2 run's to
+    the batched launch: both stay bit-identical to solo runs."""
+    runs = [((512, 512), 0.025, 0.05, 1.0, 0.005), ((64, 64), 0.025, 0.05, 2.0, 0.005)]
+    with chhs.Batch(runs) as b:
+        b.set_tuning(1024, 2, 2, tile=tile)
+        for q, r in enumerate(runs):
+            b.runs[q].set_phi(_phi0(r[0], q))
+        st, vb, _ = b.step(2)
+        assert all(s == chhs.CHHS_OK for s in st)
+        batched = [b.runs[q].get_state() for q in range(len(runs))]
+    for q, (shape, h, eps, gamma, dt) in enumerate(runs):
+        with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=1)) as solo:
+            solo.set_phi(_phi0(shape, q))
+            _, vs, _ = solo.step(2)
+            ref = solo.get_state()
+        assert vs == vb[q]
+        for a, c in zip(batched[q], ref):
+            assert np.array_equal(a, c), q
