@@ -223,15 +223,15 @@ typedef struct {
   int tail_cells;     /* levels with at most this many cells run in the one-block tail */
   int split_threads;  /* double-precision levels with at most this many cells per colour
                          use the three-warp split update (0: never) */
-  int tile_threads;   /* threads per tile in the 2D mixed form */
+  int tile_threads;   /* threads per tile on the 2D mixed form's levels of at least 512 x 256 cells */
   int coarse_nu1;     /* pre- and post-smoothing sweeps on the levels below the finest (the finest */
   int coarse_nu2;     /* keeps opts->nu1, nu2) */
-  int tile_w, tile_h; /* interior of a tile in the 2D mixed form (even; default 32 x 16) */
+  int tile_w, tile_h; /* interior of a tile on those levels (even; default 32 x 32 on 512 threads) */
   int norm_f64_per8;  /* mixed form, double-single residual: of every 8 tiles of the residual
                          kernel, how many use double-precision instructions (0..8; default 3), so
                          that the FP64 pipe works beside the single-precision ones */
-  int coarse_tile_w, coarse_tile_h; /* 2D mixed form: tile interior on the levels below the finest */
-  int coarse_tile_threads;          /* (default 16 x 8 cells on 256 threads) and its block size */
+  int small_tile_w, small_tile_h; /* 2D mixed form: tile interior on the smaller levels */
+  int small_tile_threads;         /* (default 16 x 8 cells on 256 threads) and its block size */
   double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
                          the setting in force was timed (every candidate failed, or the fastest
                          could not be rebuilt and the original setting was kept) */
@@ -240,8 +240,9 @@ typedef struct {
 /* Autotuner of the handle's launch shapes and coarse sweep counts: tries
  * candidate settings (where the one-block tail starts; in double precision,
  * up to which level size the split update is used; in the 2D mixed form, the
- * tile block size and tile shape, 32 x 16, 32 x 32 or 64 x 16 cells, and on
- * the levels below the finest the same shape or 16 x 8 cells on 256 threads; the
+ * tile block size and tile shape on levels of at least 512 x 256 cells, 32 x
+ * 16, 32 x 32 or 64 x 16 cells, and on the smaller levels the same shape or
+ * 16 x 8 cells on 256 threads; the
  * sweeps on the levels below the finest: the options' nu1, nu2 or, when both
  * exceed 1, one each), times
  * trial_steps steps of the handle's own problem from its current state with
@@ -261,7 +262,7 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out);
  * state is kept.  Errors: CHHS_ERR_INVALID_ARG (NULL, steps pending, a run
  * of a batch, tail_cells < 1, split_threads < 0, tile_threads not a multiple
  * of 32 in 32..1024, coarse sweep counts < 0 or both 0, tile sides odd or
- * below 2, tiles over 4096 cells (the same for coarse_tile_*), norm_f64_per8
+ * below 2, tiles over 4096 cells (the same for small_tile_*), norm_f64_per8
  * outside 0..8, or a setting
  * the grid cannot take -- the
  * previous tuning is then kept), CHHS_ERR_CUDA. */

@@ -61,8 +61,8 @@ class Tuning(ctypes.Structure):
     """chhs_tuning (include/chhs.h)."""
     _fields_ = [("tail_cells", ctypes.c_int), ("split_threads", ctypes.c_int), ("tile_threads", ctypes.c_int),
                 ("coarse_nu1", ctypes.c_int), ("coarse_nu2", ctypes.c_int), ("tile_w", ctypes.c_int),
-                ("tile_h", ctypes.c_int), ("norm_f64_per8", ctypes.c_int), ("coarse_tile_w", ctypes.c_int),
-                ("coarse_tile_h", ctypes.c_int), ("coarse_tile_threads", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("tile_h", ctypes.c_int), ("norm_f64_per8", ctypes.c_int), ("small_tile_w", ctypes.c_int),
+                ("small_tile_h", ctypes.c_int), ("small_tile_threads", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
 
 
 class ChhsError(RuntimeError):
@@ -339,16 +339,17 @@ class Run:
         self._check(lib().chhs_autotune(self.handle, int(trial_steps), ctypes.byref(t)))
         return dict(tail_cells=t.tail_cells, split_threads=t.split_threads, tile_threads=t.tile_threads,
                     coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2, tile_w=t.tile_w, tile_h=t.tile_h,
-                    norm_f64_per8=t.norm_f64_per8, coarse_tile=(t.coarse_tile_w, t.coarse_tile_h,
-                                                                 t.coarse_tile_threads),
+                    norm_f64_per8=t.norm_f64_per8, small_tile=(t.small_tile_w, t.small_tile_h,
+                                                                 t.small_tile_threads),
                     ms_per_step=t.ms_per_step)
 
-    def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2, tile_w=32, tile_h=16,
-                   norm_f64_per8=3, coarse_tile=(16, 8, 256)):
+    def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2, tile_w=32, tile_h=32,
+                   norm_f64_per8=3, small_tile=(16, 8, 256)):
         """chhs_set_tuning: apply launch shapes and coarse sweep counts
-        (coarse_tile: (width, height, threads) of the 2D mixed form's tiles
-        below the finest level)."""
-        cw, ch, ct = coarse_tile
+        (tile_w, tile_h, tile_threads: the 2D mixed form's tiles on levels of
+        at least 512 x 256 cells; small_tile: (width, height, threads) on the
+        smaller levels)."""
+        cw, ch, ct = small_tile
         t = Tuning(int(tail_cells), int(split_threads), int(tile_threads), int(coarse_nu1), int(coarse_nu2),
                    int(tile_w), int(tile_h), int(norm_f64_per8), int(cw), int(ch), int(ct), 0.0)
         self._check(lib().chhs_set_tuning(self.handle, ctypes.byref(t)))

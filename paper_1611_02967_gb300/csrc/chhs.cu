@@ -75,11 +75,16 @@ int level_fields(int dim, bool single) {
 // arithmetic, so that both kinds of pipes are busy (chhs_norm_df.cuh).
 constexpr int kNormF64Per8 = 3;
 
-// Tiles of the 2D single-precision levels below the finest (chhs_tuning's
-// coarse_tile_*): 16 x 8 cells on 256 threads measured 4% faster per 512^2
-// mixed-form step than the finest level's 32 x 16 on 512 (more blocks on the
-// levels of 256^2 and less; the finest level keeps its wider tiles).
-constexpr int kCoarseTileW = 16, kCoarseTileH = 8, kCoarseTileThreads = 256;
+// Tiles of the 2D single-precision levels: a level of at least
+// kLargeTileCells cells takes chhs_tuning's tile_* (default 32 x 32 cells on
+// 512 threads), a smaller one small_tile_* (default 16 x 8 on 256: four times
+// the blocks on the small, latency-bound levels).  On the 512^2 mixed step
+// 16 x 8 below the finest level measured 4% faster than 32 x 16 there, and
+// 32 x 32 on levels of 256 x 512 cells and more took the batched
+// configuration's large runs from 6.3e8 to 7.2e8 cell-steps/s.
+constexpr int kLargeTileW = 32, kLargeTileH = 32, kLargeTileThreads = 512;
+constexpr int kSmallTileW = 16, kSmallTileH = 8, kSmallTileThreads = 256;
+constexpr int kLargeTileCells = 512 * 256;
 
 // Levels with at most this many cells run inside the one-block tail kernel.
 // In double precision one SM does 2 FMA per clock and a single warp's
@@ -197,13 +202,14 @@ struct chhs {
   // most tail_cells cells go to the tail, double-precision levels of at most
   // split_threads threads per colour pass use the split update, tiles run
   // tile_threads threads
-  int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kTileThreads;
+  int tail_cells = 0, split_threads = kSplitThreads, tile_threads = kLargeTileThreads;
   int norm_blocks = 1;              // grid of the stopping-norm kernels (whole blocks per SM)
   int nu1c = 2, nu2c = 2;           // sweeps on the levels below the finest (chhs_autotune; opts by default)
-  int tile_w = kTileW, tile_h = kTileH;  // tile interior of the 2D single-precision finest level (chhs_autotune)
-  // ... and of the levels below it, with its block size: smaller tiles there
-  // make more blocks on the small, latency-bound levels
-  int ctile_w = kCoarseTileW, ctile_h = kCoarseTileH, ctile_threads = kCoarseTileThreads;
+  // tile interiors of the 2D single-precision levels of at least
+  // kLargeTileCells cells (tile_*) and of the smaller ones (stile_*, with its
+  // block size; chhs_autotune)
+  int tile_w = kLargeTileW, tile_h = kLargeTileH;
+  int stile_w = kSmallTileW, stile_h = kSmallTileH, stile_threads = kSmallTileThreads;
   int norm_f64_per8 = kNormF64Per8;      // blocks of 8 whose residual runs on the FP64 pipe (mixed form)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
@@ -359,8 +365,9 @@ struct Enqueue {
     if constexpr (use_tiles<T>()) {
       // 2D single precision: pre-smoothing (+ right-hand side) + residual +
       // restriction in one tiled launch, prolongation + post-smoothing in another
-      const int tw = l == 0 ? run->tile_w : run->ctile_w, th = l == 0 ? run->tile_h : run->ctile_h;
-      const int tt = l == 0 ? run->tile_threads : run->ctile_threads;
+      const bool large = L.ncell >= kLargeTileCells;
+      const int tw = large ? run->tile_w : run->stile_w, th = large ? run->tile_h : run->stile_h;
+      const int tt = large ? run->tile_threads : run->stile_threads;
       const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
       const int nf = tile_nfields<CORR>();
       const int np1 = 2 * nu_pre(run, l), np2 = 2 * nu_post(run, l);
@@ -517,7 +524,7 @@ struct Enqueue {
     if constexpr (use_tiles<T>()) {
       const int halo = 2 * std::max(std::max(run->opts.nu1, run->opts.nu2), std::max(run->nu1c, run->nu2c)) + 1;
       const size_t tb = std::max(tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->tile_w, run->tile_h),
-                                 tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->ctile_w, run->ctile_h));
+                                 tile_smem_bytes(halo, tile_nfields<CORR>(), sizeof(T), run->stile_w, run->stile_h));
       const void* ktile = reinterpret_cast<const void*>(k_tile<T, CORR>);
       if (!fits(ktile, tb))
         return fail(run, CHHS_ERR_INVALID_ARG, "nu1/nu2 too large for the single-precision tiles");
@@ -951,9 +958,9 @@ chhs_tuning current_tuning(const chhs_t* run) {
   t.tile_w = run->tile_w;
   t.tile_h = run->tile_h;
   t.norm_f64_per8 = run->norm_f64_per8;
-  t.coarse_tile_w = run->ctile_w;
-  t.coarse_tile_h = run->ctile_h;
-  t.coarse_tile_threads = run->ctile_threads;
+  t.small_tile_w = run->stile_w;
+  t.small_tile_h = run->stile_h;
+  t.small_tile_threads = run->stile_threads;
   t.ms_per_step = -1.0;
   return t;
 }
@@ -967,9 +974,9 @@ void take_tuning(chhs_t* run, const chhs_tuning& t) {
   run->tile_w = t.tile_w;
   run->tile_h = t.tile_h;
   run->norm_f64_per8 = t.norm_f64_per8;
-  run->ctile_w = t.coarse_tile_w;
-  run->ctile_h = t.coarse_tile_h;
-  run->ctile_threads = t.coarse_tile_threads;
+  run->stile_w = t.small_tile_w;
+  run->stile_h = t.small_tile_h;
+  run->stile_threads = t.small_tile_threads;
 }
 
 chhs_status copy_in(chhs_t* run, double* dst, const double* src, int on_device) {
@@ -1208,14 +1215,16 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
   const int blocks = (threads + kSmoothBlock - 1) / kSmoothBlock;
   const int np1 = 2 * run->opts.nu1;
   const TileOut<float> to_copy{L.phi2, L.mu2, L.p2, L.fc1, L.fc2, L.fc3, nullptr, nullptr, nullptr};
-  const int tw = run->tile_w, th = run->tile_h;
+  const bool large = L.ncell >= kLargeTileCells;
+  const int tw = large ? run->tile_w : run->stile_w, th = large ? run->tile_h : run->stile_h;
+  const int tt = large ? run->tile_threads : run->stile_threads;
   const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
   for (int k = 0; k <= npasses; ++k) {
     if (k == 1) CU(cudaEventRecord(ev.a, run->stream));
     if (run->dim == 3)
       pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
     else
-      pdl_grid(k_tile<float, true>, grid, run->tile_threads, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4, tw, th),
+      pdl_grid(k_tile<float, true>, grid, tt, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4, tw, th),
                run->stream, L, C, K, np1, np1 + 1, 0, 0, 1, to_copy, (const int*)nullptr, tw, th);
   }
   CU(cudaGetLastError());
@@ -1280,7 +1289,7 @@ chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
   };
   if (t->tail_cells < 1 || t->split_threads < 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 ||
       t->coarse_nu1 + t->coarse_nu2 < 1 || !tile_ok(t->tile_w, t->tile_h, t->tile_threads) ||
-      !tile_ok(t->coarse_tile_w, t->coarse_tile_h, t->coarse_tile_threads) || t->norm_f64_per8 < 0 ||
+      !tile_ok(t->small_tile_w, t->small_tile_h, t->small_tile_threads) || t->norm_f64_per8 < 0 ||
       t->norm_f64_per8 > 8)
     return fail(run, CHHS_ERR_INVALID_ARG, "invalid tuning");
   run->norm_f64_per8 = t->norm_f64_per8;
@@ -1322,9 +1331,9 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     c.coarse_nu2 = n2;
     c.tile_w = tw;
     c.tile_h = th;
-    c.coarse_tile_w = ctw;
-    c.coarse_tile_h = cth;
-    c.coarse_tile_threads = ctt;
+    c.small_tile_w = ctw;
+    c.small_tile_h = cth;
+    c.small_tile_threads = ctt;
     cands.push_back(c);
   };
   const bool mixed = run->opts.precision == 1;
@@ -1339,15 +1348,15 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
     int tt, tw, th;
   };
   const Shape2 shapes[4] = {{256, 32, 16}, {512, 32, 16}, {512, 32, 32}, {512, 64, 16}};
-  // the levels below the finest: the finest level's shape, or the small one
-  const Shape2 small{kCoarseTileThreads, kCoarseTileW, kCoarseTileH};
+  // the levels under kLargeTileCells: the same shape, or the small one
+  const Shape2 small{kSmallTileThreads, kSmallTileW, kSmallTileH};
   for (const auto& cn : coarse) {
     if (!mixed) {
       const int tails[2] = {64, run->dim == 2 ? 256 : 512};
       for (int tc : tails)
         for (int sp : {0, 8192, 32768})
-          cand(tc, sp, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h, run->ctile_w, run->ctile_h,
-               run->ctile_threads);
+          cand(tc, sp, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h, run->stile_w, run->stile_h,
+               run->stile_threads);
     } else if (run->dim == 2) {
       for (int tc : {256, 1024, 2048})
         for (const Shape2& sh : shapes)
@@ -1355,8 +1364,8 @@ chhs_status chhs_autotune(chhs_t* run, int trial_steps, chhs_tuning* out) {
             cand(tc, run->split_threads, sh.tt, cn.first, cn.second, sh.tw, sh.th, cs.tw, cs.th, cs.tt);
     } else {
       for (int tc : {64, 512})
-        cand(tc, run->split_threads, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h, run->ctile_w,
-             run->ctile_h, run->ctile_threads);
+        cand(tc, run->split_threads, run->tile_threads, cn.first, cn.second, run->tile_w, run->tile_h, run->stile_w,
+             run->stile_h, run->stile_threads);
     }
   }
   // the run's state (phi^m, phi^{m-1}, mu, p), restored before every trial and at the end
@@ -2422,9 +2431,9 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
     out->tile_w = b->big_tw;
     out->tile_h = b->big_th;
     out->norm_f64_per8 = r->norm_f64_per8;
-    out->coarse_tile_w = kTileW;
-    out->coarse_tile_h = kTileH;
-    out->coarse_tile_threads = kTileThreads;
+    out->small_tile_w = kTileW;
+    out->small_tile_h = kTileH;
+    out->small_tile_threads = kTileThreads;
     out->ms_per_step = best_ms < 0.f ? -1.0 : best_ms / trial_steps;
   }
   return CHHS_OK;

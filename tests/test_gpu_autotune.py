@@ -29,7 +29,7 @@ def test_autotune_keeps_state_and_steps_match_oracle(shape, precision):
         elif len(shape) == 2:
             assert t["tail_cells"] in (256, 1024, 2048) and t["tile_threads"] in (256, 512)
             assert (t["tile_w"], t["tile_h"]) in ((32, 16), (32, 32), (64, 16))
-            assert t["coarse_tile"] in ((t["tile_w"], t["tile_h"], t["tile_threads"]), (16, 8, 256))
+            assert t["small_tile"] in ((t["tile_w"], t["tile_h"], t["tile_threads"]), (16, 8, 256))
         else:
             assert t["tail_cells"] in (64, 512)
         assert (t["coarse_nu1"], t["coarse_nu2"]) in ((2, 2), (1, 1))
@@ -62,17 +62,17 @@ def test_one_coarse_sweep_reaches_the_same_answer(shape, precision):
         _check_step(run, h, eps, gamma, dt, PHI_TOL[precision])
 
 
-def test_coarse_tile_shape_changes_no_result():
-    """The tiles of the levels below the finest (chhs_tuning.coarse_tile_*)
-    only change how the colour passes are cut into blocks: the same steps
-    with 16 x 8 tiles on 256 threads and with 32 x 16 on 512 are equal bit
-    for bit (2D mixed form)."""
+def test_small_tile_shape_changes_no_result():
+    """The tiles of the levels under 512 x 256 cells (chhs_tuning.small_tile_*;
+    here every level of a 256^2 run) only change how the colour passes are
+    cut into blocks: the same steps with 16 x 8 tiles on 256 threads, 32 x
+    16 on 512 and 8 x 8 on 64 are equal bit for bit (2D mixed form)."""
     shape, h, eps, gamma, dt = (256, 256), 0.025, 0.05, 1.0, 0.005
     phi0 = inputs.spinodal(shape, 47, mean=0.0, amplitude=0.05)
     out = []
     for ct in ((16, 8, 256), (32, 16, 512), (8, 8, 64)):
         with chhs.Run(shape, h, eps, gamma, dt, opts=chhs.default_opts(precision=1)) as run:
-            run.set_tuning(1024, 8192, 512, 1, 1, 32, 16, 3, coarse_tile=ct)
+            run.set_tuning(1024, 8192, 512, 1, 1, 32, 16, 3, small_tile=ct)
             run.set_phi(phi0)
             _, v, _ = run.step(3)
             out.append((v, run.get_state()))
