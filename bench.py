@@ -454,8 +454,9 @@ def bubbles_leg(stream, flush, steps=10, warmup=3):
             alg = SMOOTH_BYTES_F32_PER_CELL_PER_COLOUR * ncell
             gbs, src = hbm_peak()
             out[key]["roofline"] = {
-                "bound": "hbm", "kernel": "k_smooth_c<3> on the 128^3 level (single-precision colour pass, "
-                                          "coefficients recomputed from phi*)",
+                "bound": "hbm", "kernel": ("k_smooth_c4<0,0>" if tune.get("quad_passes", 1) else "k_smooth_c<3>")
+                + " on the 128^3 level (single-precision colour pass, coefficients recomputed from phi*"
+                + (", four cells of a row per thread)" if tune.get("quad_passes", 1) else ")"),
                 "achieved": alg / t / 1e9, "peak": gbs, "unit": "GB/s", "frac": alg / t / 1e9 / gbs,
                 "peak_source": src, "traffic": measured_traffic(TRAFFIC_FILE_3D, KERNEL_SRC_3D),
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": 1e6 * t,

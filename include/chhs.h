@@ -232,6 +232,11 @@ typedef struct {
                          that the FP64 pipe works beside the single-precision ones */
   int small_tile_w, small_tile_h; /* 2D mixed form: tile interior on the smaller levels */
   int small_tile_threads;         /* (default 16 x 8 cells on 256 threads) and its block size */
+  int quad_passes;    /* 3D mixed form: 1 (default) runs the colour passes of levels whose x extent
+                         is a multiple of 4 with one thread per four cells of a row (16-byte loads),
+                         0 with one thread per cell; the results are the same bit for bit.  Not 0
+                         or 1: CHHS_ERR_INVALID_ARG.  A batch's runs always take one cell per thread
+                         (chhs_batch_autotune reports 0; chhs_batch_set_tuning ignores it). */
   double ms_per_step; /* the chosen setting's time per step in the trials; -1 when no trial of
                          the setting in force was timed (every candidate failed, or the fastest
                          could not be rebuilt and the original setting was kept) */

@@ -62,7 +62,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("tail_cells", ctypes.c_int), ("split_threads", ctypes.c_int), ("tile_threads", ctypes.c_int),
                 ("coarse_nu1", ctypes.c_int), ("coarse_nu2", ctypes.c_int), ("tile_w", ctypes.c_int),
                 ("tile_h", ctypes.c_int), ("norm_f64_per8", ctypes.c_int), ("small_tile_w", ctypes.c_int),
-                ("small_tile_h", ctypes.c_int), ("small_tile_threads", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("small_tile_h", ctypes.c_int), ("small_tile_threads", ctypes.c_int), ("quad_passes", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double)]
 
 
 class ChhsError(RuntimeError):
@@ -341,17 +342,18 @@ class Run:
                     coarse_nu1=t.coarse_nu1, coarse_nu2=t.coarse_nu2, tile_w=t.tile_w, tile_h=t.tile_h,
                     norm_f64_per8=t.norm_f64_per8, small_tile=(t.small_tile_w, t.small_tile_h,
                                                                  t.small_tile_threads),
-                    ms_per_step=t.ms_per_step)
+                    quad_passes=t.quad_passes, ms_per_step=t.ms_per_step)
 
     def set_tuning(self, tail_cells, split_threads, tile_threads, coarse_nu1, coarse_nu2, tile_w=32, tile_h=32,
-                   norm_f64_per8=3, small_tile=(16, 8, 256)):
+                   norm_f64_per8=3, small_tile=(16, 8, 256), quad_passes=1):
         """chhs_set_tuning: apply launch shapes and coarse sweep counts
         (tile_w, tile_h, tile_threads: the 2D mixed form's tiles on levels of
         at least 512 x 256 cells; small_tile: (width, height, threads) on the
-        smaller levels)."""
+        smaller levels; quad_passes: the 3D mixed form's colour passes on four
+        cells per thread (1) or one (0))."""
         cw, ch, ct = small_tile
         t = Tuning(int(tail_cells), int(split_threads), int(tile_threads), int(coarse_nu1), int(coarse_nu2),
-                   int(tile_w), int(tile_h), int(norm_f64_per8), int(cw), int(ch), int(ct), 0.0)
+                   int(tile_w), int(tile_h), int(norm_f64_per8), int(cw), int(ch), int(ct), int(quad_passes), 0.0)
         self._check(lib().chhs_set_tuning(self.handle, ctypes.byref(t)))
 
     def mass(self):
@@ -532,7 +534,7 @@ class Batch:
         tile launches of large 2D levels; rebuilds the batch's graph."""
         tw, th, tt = tile
         t = Tuning(int(tail_cells), 0, int(tt), int(coarse_nu1), int(coarse_nu2), int(tw), int(th), int(norm_f64_per8),
-                   32, 16, kTileThreads, 0.0)
+                   32, 16, kTileThreads, 0, 0.0)
         self._check(lib().chhs_batch_set_tuning(self.handle, ctypes.byref(t)), "chhs_batch_set_tuning")
 
     def autotune(self, trial_steps=2):

@@ -211,6 +211,7 @@ struct chhs {
   int tile_w = kLargeTileW, tile_h = kLargeTileH;
   int stile_w = kSmallTileW, stile_h = kSmallTileH, stile_threads = kSmallTileThreads;
   int norm_f64_per8 = kNormF64Per8;      // blocks of 8 whose residual runs on the FP64 pipe (mixed form)
+  int quad_passes = 1;              // 3D mixed form: x-quad colour passes where nx % 4 == 0 (k_smooth_c4)
   Tail<double> tail{};              // its levels (double-precision V-cycles)
   Tail<float> tail32{};             // (single-precision inner V-cycles)
   double* phimm1 = nullptr;
@@ -447,11 +448,28 @@ struct Enqueue {
     const int kind = l == 0 ? CHHS_K_SMOOTH_FINEST : CHHS_K_SMOOTH;
     const Level<double> none{};
     const int nu1 = nu_pre(run, l), nu2 = nu_post(run, l);
+    // one colour pass: x-quads (k_smooth_c4, the same results bit for bit)
+    // where the rows split into whole quads, else one cell per thread
+    auto pass = [&](int colour, int with_rhs, int pro, const Level<double>& U) {
+      if constexpr (DIM == 3) {
+        if (quad_level(run, L)) {
+          const int qb = (int)(((long long)(L.nx / 4) * L.ny * L.nz + kSmoothBlock - 1) / kSmoothBlock);
+          if (with_rhs)
+            pdl(k_smooth_c4<1, 0>, qb, kSmoothBlock, s, L, C, K, colour, U);
+          else if (pro == 1)
+            pdl(k_smooth_c4<0, 1>, qb, kSmoothBlock, s, L, C, K, colour, U);
+          else if (pro == 2)
+            pdl(k_smooth_c4<0, 2>, qb, kSmoothBlock, s, L, C, K, colour, U);
+          else
+            pdl(k_smooth_c4<0, 0>, qb, kSmoothBlock, s, L, C, K, colour, U);
+          return;
+        }
+      }
+      pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, with_rhs, pro, U);
+    };
     for (int it = 0; it < nu1; ++it)
       for (int colour = 0; colour < 2; ++colour)
-        launch(run, s, kind, colour_cells(L, colour), [&] {
-          pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, (rhs && it == 0) ? 1 : 0, 0, none);
-        });
+        launch(run, s, kind, colour_cells(L, colour), [&] { pass(colour, (rhs && it == 0) ? 1 : 0, 0, none); });
     const long long warps = rr_c_warps(DIM, L.nx, L.ny, L.nz);
     const int rblocks = (int)((warps * 32 + kBlock - 1) / kBlock);
     launch(run, s, CHHS_K_RESTRICT, L.ncell, [&] {
@@ -468,13 +486,16 @@ struct Enqueue {
       for (int colour = 0; colour < 2; ++colour) {
         const int pro = it == 0 ? (colour == 0 ? 1 : 2) : 0;
         const bool upd = l == 0 && fused_update(run) && run->vc_update && it == nu2 - 1 && colour == 1;
-        launch(run, s, kind, colour_cells(L, colour), [&] {
-          pdl(k_smooth_c<DIM>, blocks, kSmoothBlock, s, L, C, K, colour, 0, pro, upd ? run->lev[0] : none);
-        });
+        launch(run, s, kind, colour_cells(L, colour), [&] { pass(colour, 0, pro, upd ? run->lev[0] : none); });
       }
   }
 
   static bool mixed(const chhs_t* run) { return run->opts.precision == 1; }
+
+  // A 3D single-precision level whose colour passes run as x-quads.
+  static bool quad_level(const chhs_t* run, const Level<float>& L) {
+    return DIM == 3 && run->quad_passes && L.nx % 4 == 0;
+  }
 
   // Mixed form whose finest level is not in the tail: the last smoothing
   // launch of a V-cycle performs the update u <- u + e (the 2D tile, or in 3D
@@ -961,6 +982,7 @@ chhs_tuning current_tuning(const chhs_t* run) {
   t.small_tile_w = run->stile_w;
   t.small_tile_h = run->stile_h;
   t.small_tile_threads = run->stile_threads;
+  t.quad_passes = run->quad_passes;
   t.ms_per_step = -1.0;
   return t;
 }
@@ -977,6 +999,7 @@ void take_tuning(chhs_t* run, const chhs_tuning& t) {
   run->stile_w = t.small_tile_w;
   run->stile_h = t.small_tile_h;
   run->stile_threads = t.small_tile_threads;
+  run->quad_passes = t.quad_passes;
 }
 
 chhs_status copy_in(chhs_t* run, double* dst, const double* src, int on_device) {
@@ -1221,7 +1244,10 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
   const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
   for (int k = 0; k <= npasses; ++k) {
     if (k == 1) CU(cudaEventRecord(ev.a, run->stream));
-    if (run->dim == 3)
+    if (run->dim == 3 && run->quad_passes && L.nx % 4 == 0)
+      pdl(k_smooth_c4<0, 0>, (int)(((long long)(L.nx / 4) * L.ny * L.nz + kSmoothBlock - 1) / kSmoothBlock),
+          kSmoothBlock, run->stream, L, C, K, k & 1, Level<double>{});
+    else if (run->dim == 3)
       pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
     else
       pdl_grid(k_tile<float, true>, grid, tt, tile_smem_bytes(np1 + 1, tile_nfields<true>(), 4, tw, th),
@@ -1290,7 +1316,7 @@ chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
   if (t->tail_cells < 1 || t->split_threads < 0 || t->coarse_nu1 < 0 || t->coarse_nu2 < 0 ||
       t->coarse_nu1 + t->coarse_nu2 < 1 || !tile_ok(t->tile_w, t->tile_h, t->tile_threads) ||
       !tile_ok(t->small_tile_w, t->small_tile_h, t->small_tile_threads) || t->norm_f64_per8 < 0 ||
-      t->norm_f64_per8 > 8)
+      t->norm_f64_per8 > 8 || (t->quad_passes != 0 && t->quad_passes != 1))
     return fail(run, CHHS_ERR_INVALID_ARG, "invalid tuning");
   run->norm_f64_per8 = t->norm_f64_per8;
   run->err.clear();
@@ -2434,6 +2460,7 @@ chhs_status chhs_batch_autotune(chhs_batch_t* b, int trial_steps, chhs_tuning* o
     out->small_tile_w = kTileW;
     out->small_tile_h = kTileH;
     out->small_tile_threads = kTileThreads;
+    out->quad_passes = 0;
     out->ms_per_step = best_ms < 0.f ? -1.0 : best_ms / trial_steps;
   }
   return CHHS_OK;

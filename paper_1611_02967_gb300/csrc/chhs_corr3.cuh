@@ -115,6 +115,23 @@ __device__ __forceinline__ void n_corr(const Level<float>& L, const Coefs<float>
   n3 = -L.ih2 * ((sp - mm * u.p) + K.gamma * (amu - F.sa * u.mu));
 }
 
+// The cell's Newton step in correction form from its residual rows R1, R2,
+// R3 (the pressure row eliminated, as in cell_update): the updated values.
+template <int DIM>
+__device__ __forceinline__ Val3 corr_newton(const Level<float>& L, const Coefs<float>& K, const FacesC<DIM>& F,
+                                            const Val3& u, float phib, float pm, float R1, float R2, float R3) {
+  const float im = rcp_approx((float)F.m);
+  const float R3n = L.h2 * im * R3;
+  const float w = phib + u.phi;
+  const float B = (0.75f * w + 0.5f * pm) * w + 0.25f * pm * pm + L.e34ih2 * (float)F.m;
+  const float Ae = L.sih2 * (F.sM - K.gamma * F.sa * F.sa * im);
+  const float Cc = L.sih2 * F.sa, Gn = K.gamma * F.sa * im;
+  const float dphi = ((R1 - Ae * R2) - Cc * R3n) * rcp_approx(1.f + Ae * B);
+  const float dmu = R2 + B * dphi;
+  const float dp = R3n - Gn * dmu;
+  return Val3{u.phi + dphi, u.mu + dmu, u.p + dp};
+}
+
 // One colour pass of the correction-form smoother on a single-precision
 // level with recomputed coefficients (the update of cell_update: a Newton
 // step on the cell's (phi, mu, p) with the pressure row eliminated).
@@ -173,17 +190,8 @@ __device__ __forceinline__ void smooth_c_body(int bx, const Level<float>& L, con
     }
     float n1, n2, n3;
     n_corr<DIM>(L, K, F, u, nb, phib, pm, n1, n2, n3);
-    const float R1 = f1 - n1, R2 = f2 - n2;
-    const float im = rcp_approx((float)F.m);
-    const float R3n = L.h2 * im * (f3 - n3);
-    const float w = phib + u.phi;
-    const float B = (0.75f * w + 0.5f * pm) * w + 0.25f * pm * pm + L.e34ih2 * (float)F.m;
-    const float Ae = L.sih2 * (F.sM - K.gamma * F.sa * F.sa * im);
-    const float Cc = L.sih2 * F.sa, Gn = K.gamma * F.sa * im;
-    const float dphi = ((R1 - Ae * R2) - Cc * R3n) * rcp_approx(1.f + Ae * B);
-    const float dmu = R2 + B * dphi;
-    const float dp = R3n - Gn * dmu;
-    const float ephi = u.phi + dphi, emu = u.mu + dmu, ep = u.p + dp;
+    const Val3 e = corr_newton<DIM>(L, K, F, u, phib, pm, f1 - n1, f2 - n2, f3 - n3);
+    const float ephi = e.phi, emu = e.mu, ep = e.p;
     L.phi[c] = ephi;
     L.mu[c] = emu;
     L.p[c] = ep;
@@ -213,10 +221,9 @@ __global__ void __launch_bounds__(kSmoothBlock, 8) k_smooth_c(const __grid_const
   smooth_c_body<DIM>(blockIdx.x, L, C, K, colour, rhs, pro, U);
 }
 
-// ---------------------------------------------------------------- restriction
-
 // Face data of a cell from its phi* value pc and its neighbours' pe[] (the
-// cell's own value where in[q] is false), as faces_c forms it from indices.
+// cell's own value where in[q] is false), as faces_c forms it from indices
+// (the x-quad passes and the restriction).
 template <int DIM>
 __device__ __forceinline__ void faces_vals(const Coefs<float>& K, float pc, const float (&pe)[6], const bool (&in)[6],
                                            FacesC<DIM>& F) {
@@ -236,6 +243,237 @@ __device__ __forceinline__ void faces_vals(const Coefs<float>& K, float pc, cons
     F.in |= in[q] ? (1u << q) : 0u;
   }
 }
+
+// ------------------------------------------------------------ x-quad passes
+//
+// The 3D colour pass above with each lane on four consecutive cells of a row,
+// 4q .. 4q+3, on levels whose nx is a multiple of 4.  The lane updates the two
+// cells of the pass's colour among them, 4q+s and 4q+s+2 (s = (j + k +
+// colour) & 1), and reads every field as 16-byte vectors: the quad, the quads
+// beside it in y and z, and the one x neighbour outside the quad (4q-1 when
+// s = 0, 4q+4 when s = 1) as a single value -- 6 load instructions per field
+// for two updated cells where one cell per lane takes 7 for one, and the
+// index arithmetic shared by both.  Each cell's arithmetic is that of
+// smooth_c_body in the same order, missing faces included (the cell's own
+// value under a zero coefficient), so the results are the same bit for bit.
+// The state is written back as whole quads, the other colour's cells with
+// the values the pass read (unchanged in memory during the pass).
+
+// A field's values around an x-quad: the quad (o), the quads beside it in y
+// and z (the quad itself on a missing face) and the outside x neighbour (e;
+// the cell itself at the domain's end).
+struct Quad {
+  float4 o, ym, yp, zm, zp;
+  float e;
+};
+
+struct QuadAt {
+  int c4;       // first cell of the quad (a multiple of 4)
+  int sy, sz;   // strides of y and z
+  int xe;       // index of the outside x neighbour
+  int s;        // the pass's cells are 4q+s and 4q+s+2
+  bool ym, yp, zm, zp, xin;  // faces present; xin: the outside x neighbour exists
+};
+
+__device__ __forceinline__ float4 ld4(const float* a, int x) { return *reinterpret_cast<const float4*>(a + x); }
+
+__device__ __forceinline__ Quad load_quad(const float* a, const QuadAt& Q) {
+  Quad r;
+  r.o = ld4(a, Q.c4);
+  r.ym = Q.ym ? ld4(a, Q.c4 - Q.sy) : r.o;
+  r.yp = Q.yp ? ld4(a, Q.c4 + Q.sy) : r.o;
+  r.zm = Q.zm ? ld4(a, Q.c4 - Q.sz) : r.o;
+  r.zp = Q.zp ? ld4(a, Q.c4 + Q.sz) : r.o;
+  r.e = Q.xin ? a[Q.xe] : (Q.s ? r.o.w : r.o.x);
+  return r;
+}
+
+// Coarse cells of the prolongation P(e_c - e_c^0) for a quad: the coarse
+// x-pair 2q, 2q+1 of the quad's row and of the rows beside it in y and z
+// (the quad's own where a face is missing), and of the outside x neighbour.
+struct QuadCoarse {
+  int o, ym, yp, zm, zp, e;
+};
+
+__device__ __forceinline__ float2 coarse_diff2(const float* cn, const float* c0, int x) {
+  const float2 a = *reinterpret_cast<const float2*>(cn + x), b = *reinterpret_cast<const float2*>(c0 + x);
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+
+__device__ __forceinline__ void add_diff(float4& v, float2 d) {
+  v.x += d.x;
+  v.y += d.x;
+  v.z += d.y;
+  v.w += d.y;
+}
+
+// Every value of X read with the prolongation added (the first
+// post-smoothing pass); dO returns the quad's own coarse differences.
+__device__ __forceinline__ void prolong_quad(Quad& X, const float* cn, const float* c0, const QuadCoarse& P,
+                                             const QuadAt& Q, float2& dO) {
+  dO = coarse_diff2(cn, c0, P.o);
+  add_diff(X.o, dO);
+  add_diff(X.ym, coarse_diff2(cn, c0, P.ym));
+  add_diff(X.yp, coarse_diff2(cn, c0, P.yp));
+  add_diff(X.zm, coarse_diff2(cn, c0, P.zm));
+  add_diff(X.zp, coarse_diff2(cn, c0, P.zp));
+  X.e += Q.xin ? cn[P.e] - c0[P.e] : (Q.s ? dO.y : dO.x);
+}
+
+// RHS: complete the FAS right-hand side first (as rhs in smooth_c_body);
+// PRO: 1 = every value read with the prolongation added, 2 = the pass's own
+// cells only (as pro); U: as in smooth_c_body, here for all four cells of
+// the quad (the other colour's two are final since the previous pass).
+template <int RHS, int PRO>
+__device__ __forceinline__ void smooth_c4_body(int bx, const Level<float>& L, const Level<float>& C,
+                                               const Coefs<float>& K, int colour, const Level<double>& U) {
+  const int nq = L.nx >> 2;
+  const int t = bx * blockDim.x + threadIdx.x;
+  int row, k;
+  if (t < (1 << 21)) {
+    row = small_div(t, 2.f * L.rhw);  // 2 rn(1/(nx/2)) = rn(1/nq) exactly
+    k = small_div(row, L.rny);
+  } else {
+    row = t / nq;
+    k = row / L.ny;
+  }
+  if (k >= L.nz) return;
+  const int j = row - k * L.ny, q = t - row * nq;
+  QuadAt Q;
+  Q.s = (j + k + colour) & 1;
+  Q.sy = L.nx;
+  Q.sz = L.nx * L.ny;
+  Q.c4 = 4 * q + L.nx * row;
+  Q.ym = j > 0;
+  Q.yp = j + 1 < L.ny;
+  Q.zm = k > 0;
+  Q.zp = k + 1 < L.nz;
+  Q.xin = Q.s ? 4 * q + 4 < L.nx : q > 0;
+  Q.xe = Q.s ? Q.c4 + 4 : Q.c4 - 1;
+
+  const Quad S = load_quad(L.phis, Q);
+  Quad P = load_quad(L.phi, Q), M = load_quad(L.mu, Q), R = load_quad(L.p, Q);
+  const float4 pm4 = ld4(L.phim, Q.c4), pb4 = ld4(L.phib, Q.c4);
+  float4 f1 = ld4(L.fphi, Q.c4), f2 = ld4(L.fmu, Q.c4), f3 = ld4(L.fp, Q.c4);
+  Quad P0, M0, R0;
+  if (RHS) {
+    P0 = load_quad(L.phi0, Q);
+    M0 = load_quad(L.mu0, Q);
+    R0 = load_quad(L.p0, Q);
+  }
+  float4 outP = P.o, outM = M.o, outR = R.o;  // written back: the other colour's cells as read
+  float2 dP = make_float2(0.f, 0.f), dM = dP, dR = dP;
+  if (PRO) {
+    QuadCoarse Pc;
+    auto crow = [&](int jj, int kk) { return C.nx * ((jj >> 1) + C.ny * (kk >> 1)) + 2 * q; };
+    Pc.o = crow(j, k);
+    Pc.ym = crow(Q.ym ? j - 1 : j, k);
+    Pc.yp = crow(Q.yp ? j + 1 : j, k);
+    Pc.zm = crow(j, Q.zm ? k - 1 : k);
+    Pc.zp = crow(j, Q.zp ? k + 1 : k);
+    Pc.e = Pc.o + (Q.s ? 2 : -1);
+    if (PRO == 1) {
+      prolong_quad(P, C.phi, C.phi0, Pc, Q, dP);
+      prolong_quad(M, C.mu, C.mu0, Pc, Q, dM);
+      prolong_quad(R, C.p, C.p0, Pc, Q, dR);
+    } else {
+      dP = coarse_diff2(C.phi, C.phi0, Pc.o);
+      dM = coarse_diff2(C.mu, C.mu0, Pc.o);
+      dR = coarse_diff2(C.p, C.p0, Pc.o);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // the cells 4q+s, then 4q+s+2
+    auto at = [&](const float4& v) { return h ? (Q.s ? v.w : v.z) : (Q.s ? v.y : v.x); };
+    auto xm = [&](const Quad& X) { return h ? (Q.s ? X.o.z : X.o.y) : (Q.s ? X.o.x : X.e); };
+    auto xp = [&](const Quad& X) { return h ? (Q.s ? X.e : X.o.w) : (Q.s ? X.o.z : X.o.y); };
+    auto put = [&](float4& v, float x) {
+      if (h) {
+        v.w = Q.s ? x : v.w;
+        v.z = Q.s ? v.z : x;
+      } else {
+        v.y = Q.s ? x : v.y;
+        v.x = Q.s ? v.x : x;
+      }
+    };
+    auto nbs = [&](const Quad& A, const Quad& B, const Quad& D, Val3 (&nb)[6]) {
+      nb[0] = Val3{xm(A), xm(B), xm(D)};
+      nb[1] = Val3{xp(A), xp(B), xp(D)};
+      nb[2] = Val3{at(A.ym), at(B.ym), at(D.ym)};
+      nb[3] = Val3{at(A.yp), at(B.yp), at(D.yp)};
+      nb[4] = Val3{at(A.zm), at(B.zm), at(D.zm)};
+      nb[5] = Val3{at(A.zp), at(B.zp), at(D.zp)};
+    };
+    const bool in[6] = {h || Q.s || Q.xin, !h || !Q.s || Q.xin, Q.ym, Q.yp, Q.zm, Q.zp};
+    const float pe[6] = {xm(S), xp(S), at(S.ym), at(S.yp), at(S.zm), at(S.zp)};
+    FacesC<3> F;
+    faces_vals<3>(K, at(S.o), pe, in, F);
+    const float pm = at(pm4), phib = at(pb4);
+    float g1 = at(f1), g2 = at(f2), g3 = at(f3);
+    float n1, n2, n3;
+    if (RHS) {  // f += N(R u), R u = (phi0, mu0, p0) of this coarse level
+      const Val3 u0{at(P0.o), at(M0.o), at(R0.o)};
+      Val3 nb0[6];
+      nbs(P0, M0, R0, nb0);
+      n_corr<3>(L, K, F, u0, nb0, phib, pm, n1, n2, n3);
+      g1 += n1;
+      g2 += n2;
+      g3 += n3;
+      put(f1, g1);
+      put(f2, g2);
+      put(f3, g3);
+    }
+    Val3 u{at(P.o), at(M.o), at(R.o)};
+    if (PRO == 2) {
+      u.phi += h ? dP.y : dP.x;
+      u.mu += h ? dM.y : dM.x;
+      u.p += h ? dR.y : dR.x;
+    }
+    Val3 nb[6];
+    nbs(P, M, R, nb);
+    n_corr<3>(L, K, F, u, nb, phib, pm, n1, n2, n3);
+    const Val3 e = corr_newton<3>(L, K, F, u, phib, pm, g1 - n1, g2 - n2, g3 - n3);
+    put(outP, e.phi);
+    put(outM, e.mu);
+    put(outR, e.p);
+  }
+  if (RHS) {
+    *reinterpret_cast<float4*>(L.fphi + Q.c4) = f1;
+    *reinterpret_cast<float4*>(L.fmu + Q.c4) = f2;
+    *reinterpret_cast<float4*>(L.fp + Q.c4) = f3;
+  }
+  *reinterpret_cast<float4*>(L.phi + Q.c4) = outP;
+  *reinterpret_cast<float4*>(L.mu + Q.c4) = outM;
+  *reinterpret_cast<float4*>(L.p + Q.c4) = outR;
+  if (U.phi) {  // u <- u + e over the whole quad
+    auto upd = [&](double* a, const float4& v) {
+      double2* d = reinterpret_cast<double2*>(a + Q.c4);
+      double2 lo = d[0], hi = d[1];
+      lo.x += (double)v.x;
+      lo.y += (double)v.y;
+      hi.x += (double)v.z;
+      hi.y += (double)v.w;
+      d[0] = lo;
+      d[1] = hi;
+    };
+    upd(U.phi, outP);
+    upd(U.mu, outM);
+    upd(U.p, outR);
+  }
+}
+
+// Launched with (nx/4) ny nz threads.  The plain pass fits 80 registers
+// without spills (6 blocks of 128 threads per SM); the passes that also read
+// the coarse level or R u, 128 (4 blocks).
+template <int RHS, int PRO>
+__global__ void __launch_bounds__(kSmoothBlock, (RHS || PRO) ? 4 : 6) k_smooth_c4(const __grid_constant__ Level<float> L,
+                                                            const __grid_constant__ Level<float> C, Coefs<float> K,
+                                                            int colour, const __grid_constant__ Level<double> U) {
+  pdl_enter();
+  smooth_c4_body<RHS, PRO>(blockIdx.x, L, C, K, colour, U);
+}
+
+// ---------------------------------------------------------------- restriction
 
 // Warps of k_residual_restrict_c on an nx x ny (x nz) level: each covers 2 *
 // rr_c_pairs(dim) x 2 (x 2) fine cells, a lane an x-pair of them.

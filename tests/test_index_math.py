@@ -4,6 +4,7 @@
 precision is emulated with numpy float32 (round to nearest, no contraction:
 the device expression is an add followed by a multiply)."""
 import numpy as np
+import pytest
 
 
 def small_div(t, d):
@@ -69,3 +70,81 @@ def test_f64_to_f32_rz_bits():
         assert abs(x - y) <= abs(x) * 2.0 ** -23
         assert abs(float(f) - y) <= abs(x) * 2.0 ** -23
     assert emu(1e-40) == 0.0 and emu(3.0) == 3.0
+
+
+def _quad_pass_accesses(nx, ny, nz, block=128):
+    """Every thread of a k_smooth_c4 launch on an nx x ny x nz level (nx a
+    multiple of 4), with the kernel's index arithmetic restated: the quad
+    each live thread takes and every index it loads or stores, on the level
+    and on the next coarser one (nx/2 x ny/2 x nz/2)."""
+    nq = nx // 4
+    threads = nq * ny * nz
+    t = np.arange(-(-threads // block) * block, dtype=np.int64)
+    hw = nx // 2
+    rd = np.float32(2.0) * (np.float32(1.0) / np.float32(hw))  # 2 rn(1/hw)
+    rny = np.float32(1.0) / np.float32(ny)
+    small = t < (1 << 21)
+
+    def sdiv(a, r):
+        return np.trunc((a.astype(np.float32) + np.float32(0.5)) * r).astype(np.int64)
+
+    row = np.where(small, sdiv(t, rd), t // nq)
+    k = np.where(small, sdiv(row, rny), row // ny)
+    live = k < nz
+    t, row, k = t[live], row[live], k[live]
+    j = row - k * ny
+    q = t - row * nq
+    return t, q, j, k
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 128), (64, 64, 64), (32, 32, 32), (16, 16, 16), (8, 8, 8),
+                                   (64, 32, 16), (16, 8, 24), (12, 6, 10), (4, 4, 4), (256, 256, 256),
+                                   (20, 40, 8)])
+def test_quad_pass_index_map(shape):
+    """k_smooth_c4's thread-to-quad map and bounds: each quad of the level is
+    taken by exactly one live thread (the division-free quotient with
+    2 rn(1/(nx/2)) = rn(1/(nx/4)) is exact below 2^21 threads, plain division
+    above), every 16-byte vector starts at a multiple of 4 cells and lies in
+    the level, the outside x neighbour and the y/z neighbour quads are read
+    only where they exist, and the coarse pairs of the prolongation lie in
+    the coarser level and start at an even cell."""
+    nx, ny, nz = shape
+    assert nx % 4 == 0
+    t, q, j, k = _quad_pass_accesses(nx, ny, nz)
+    nq = nx // 4
+    assert np.array_equal(np.sort(q + nq * (j + ny * k)), np.arange(nq * ny * nz))
+    assert q.min() >= 0 and q.max() < nq and j.min() >= 0 and j.max() < ny
+    ncell = nx * ny * nz
+    sy, sz = nx, nx * ny
+    c4 = 4 * q + nx * (j + ny * k)
+    assert (c4 % 4 == 0).all()
+    ym, yp, zm, zp = j > 0, j + 1 < ny, k > 0, k + 1 < nz
+    for colour in (0, 1):
+        s = (j + k + colour) & 1
+        xin = np.where(s == 1, 4 * q + 4 < nx, q > 0)
+        xe = np.where(s == 1, c4 + 4, c4 - 1)
+        loads = [c4] + [c4 + d for d, ok in ((-sy, ym), (sy, yp), (-sz, zm), (sz, zp))]
+        oks = [np.ones_like(ym), ym, yp, zm, zp]
+        for a, ok in zip(loads, oks):
+            assert ((a[ok] >= 0) & (a[ok] + 3 < ncell)).all()
+        assert ((xe[xin] >= 0) & (xe[xin] < ncell)).all()
+        # the outside neighbour is the row's, and missing only at the row's ends
+        assert (xe[xin] // nx == c4[xin] // nx).all()
+        assert (~xin == np.where(s == 1, 4 * q + 4 == nx, q == 0)).all()
+        # the updated cells 4q+s, 4q+s+2 are of the pass's colour
+        for h in (0, 1):
+            i = 4 * q + s + 2 * h
+            assert ((i + j + k + colour) % 2 == 0).all() and (i < nx).all()
+        if ny % 2 == 0 and nz % 2 == 0 and nx >= 4:
+            cx, cy, cz = nx // 2, ny // 2, nz // 2
+            cn = cx * cy * cz
+
+            def crow(jj, kk):
+                return cx * ((jj >> 1) + cy * (kk >> 1)) + 2 * q
+            rows = [crow(j, k), crow(np.where(ym, j - 1, j), k), crow(np.where(yp, j + 1, j), k),
+                    crow(j, np.where(zm, k - 1, k)), crow(j, np.where(zp, k + 1, k))]
+            for a in rows:
+                assert ((a >= 0) & (a + 1 < cn) & (a % 2 == 0)).all()
+            ce = rows[0] + np.where(s == 1, 2, -1)
+            assert ((ce[xin] >= 0) & (ce[xin] < cn)).all()
+            assert (ce[xin] // cx == rows[0][xin] // cx).all()
