@@ -18,7 +18,9 @@ with nu1 = 0 the coarse right-hand side runs as its own kernel.  Each case
 runs with the one-block tail from 1024 cells (the default) and from 64, so
 that small levels (8^3: two quads per row) run as colour passes too, and the
 grid with an x extent of 20 runs its 10-cell level on one cell per thread
-beside the quad level above it.
+beside the quad level above it; the 256 x 8 x 8 grid runs long rows (whole
+warps in one row) on its finest level and, with the right-hand side
+completed, on its 128 x 4 x 4 level.
 """
 import numpy as np
 import pytest
@@ -34,6 +36,7 @@ CASES = [
     ((24, 8, 16), 0.1, 0.08, 0.0, 0.005),    # gamma = 0: the pressure decouples
     ((8, 40, 20), 0.1, 0.08, 1.0, 0.01),     # x extent 20, then 10 (one cell per thread)
     ((10, 6, 12), 0.2, 0.1, 2.0, 0.01),      # ragged coarsening (6 x 3 x 5 below)
+    ((8, 8, 256), 0.1, 0.08, 2.0, 0.005),    # x extents 256 and 128
 ]
 
 
