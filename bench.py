@@ -61,6 +61,28 @@ SMOOTH_BYTES_F64 = 72.0
 SMOOTH_BYTES_F32_PER_CELL_PER_COLOUR = 24.0
 
 
+L2_PROBE_SOURCE = ("measured: chhs_probe_l2 (48 MiB held in the L2, read 50 times by every SM with L1-bypassing "
+                   "16-byte loads, best of 3) in this run")
+
+
+def l2_peak():
+    """Measured L2 read bandwidth (GB/s) of this GPU, best of three probes."""
+    from paper_1611_02967_gb300 import chhs
+    return max(chhs.probe_l2() for _ in range(3))
+
+
+def l2_roofline(alg_bytes, secs, peak, lts_bytes, why):
+    """The kernel against the L2's read bandwidth: its algorithmic bytes, and
+    the L2 traffic ncu counted for it (lts__t_bytes, when the summary matches
+    the source), per launch over its duration."""
+    out = {"peak_gbs": peak, "peak_source": L2_PROBE_SOURCE, "algorithmic_gbs": alg_bytes / secs / 1e9,
+           "frac_algorithmic": alg_bytes / secs / 1e9 / peak, "traffic": lts_bytes, "note": why}
+    if lts_bytes:
+        out["achieved_gbs"] = lts_bytes / secs / 1e9
+        out["frac"] = lts_bytes / secs / 1e9 / peak
+    return out
+
+
 def hbm_peak():
     """(GB/s, source): the measured copy bandwidth of this GPU pool written
     beside the repository, else the recipe's fallback figure."""
@@ -155,10 +177,11 @@ def file_hash(path):
     return hashlib.sha256(src[:cut if cut > 0 else len(src)]).hexdigest()[:16]
 
 
-def measured_traffic(path=None, src=None):
-    """DRAM bytes per launch of the profiled kernel from a committed ncu
-    summary (default: the double-precision smoother's), if it was taken on
-    the current kernel source; else None."""
+def measured_traffic(path=None, src=None, key="dram_bytes_per_launch"):
+    """DRAM bytes per launch (or another per-launch figure, key) of the
+    profiled kernel from a committed ncu summary (default: the
+    double-precision smoother's), if it was taken on the current kernel
+    source; else None."""
     path = path or TRAFFIC_FILE
     try:
         vals = {}
@@ -169,7 +192,7 @@ def measured_traffic(path=None, src=None):
                     vals[k.strip()] = v.strip()
         if vals.get("kernel_source_sha256_16") != (kernel_hash() if src is None else file_hash(src)):
             return None
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -459,6 +482,9 @@ def bubbles_leg(stream, flush, steps=10, warmup=3):
                 + (", four cells of a row per thread)" if tune.get("quad_passes", 1) else ")"),
                 "achieved": alg / t / 1e9, "peak": gbs, "unit": "GB/s", "frac": alg / t / 1e9 / gbs,
                 "peak_source": src, "traffic": measured_traffic(TRAFFIC_FILE_3D, KERNEL_SRC_3D),
+                "l2": l2_roofline(alg, t, l2_peak(), measured_traffic(TRAFFIC_FILE_3D, KERNEL_SRC_3D,
+                                                                      "lts_bytes_per_launch"),
+                                  "warm, the level's nine fields (75 MB) largely stay in the L2 between passes"),
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": 1e6 * t,
                 "duration_source": "100 launches back to back between CUDA events (chhs_profile_smooth32)",
                 "note": "24 B per cell per colour launch: the twelve 4-byte values of a sweep (read correction, "
@@ -590,6 +616,7 @@ def run_ours(args):
     achieved = flops_per_launch / avg_s / 1e12
     traffic = measured_traffic()
     fp64_peak = max(chhs.probe_fp64() for _ in range(3))
+    l2_gbs = l2_peak()
     cells_per_launch = sm_units / sm_launch
     hbm_bytes = SMOOTH_BYTES_F64 * cells_per_launch
     hbm_gbs, hbm_src = hbm_peak()
@@ -602,6 +629,8 @@ def run_ours(args):
                         "peak_gbs": hbm_gbs, "peak_source": hbm_src, "frac": hbm_bytes / avg_s / 1e9 / hbm_gbs,
                         "note": "72 B per cell updated (read phi, mu, p, phi^m, phi*, f_mu; write phi, mu, p), "
                                 "the hot-path table's byte model; this kernel is bound by the FP64 pipe"},
+                "l2": l2_roofline(hbm_bytes, avg_s, l2_gbs, measured_traffic(key="lts_bytes_per_launch"),
+                                  "the 512^2 hierarchy (~55 MB) stays in the L2 between passes"),
                 "traffic": traffic, "flop_per_launch": flops_per_launch,
                 "avg_launch_us": 1e6 * avg_s, "avg_launch_us_eager": 1e3 * sm_ms / sm_launch,
                 "duration_source": "200 finest-level passes back to back between CUDA events (chhs_profile_smooth)",

@@ -218,6 +218,15 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
  * CHHS_ERR_CUDA.  No counterpart in the paper. */
 chhs_status chhs_probe_fp64(double* tflops_out);
 
+/* Measured read bandwidth of the current device's L2: a buffer of `bytes`
+ * (1 MiB up to half the L2), allocated and zeroed here, is read once to bring
+ * it into the L2 and then `passes` times by every SM with loads that bypass
+ * L1, timed with CUDA events; *gbs_out in GB/s.  The roofline denominator of
+ * kernels whose working set stays in the L2.  Errors: CHHS_ERR_INVALID_ARG
+ * (NULL, passes < 1, bytes out of range), CHHS_ERR_OOM, CHHS_ERR_CUDA.  No
+ * counterpart in the paper. */
+chhs_status chhs_probe_l2(size_t bytes, int passes, double* gbs_out);
+
 /* Launch shapes of one handle (see chhs_autotune). */
 typedef struct {
   int tail_cells;     /* levels with at most this many cells run in the one-block tail */

@@ -30,7 +30,7 @@ EXPORTS = ["chhs_default_opts", "chhs_workspace_bytes", "chhs_create", "chhs_cre
            "chhs_server_release", "chhs_server_stats", "chhs_server_destroy", "chhs_profile_smooth", "chhs_velocity",
            "chhs_autotune", "chhs_batch_workspace_bytes", "chhs_batch_create", "chhs_batch_size", "chhs_batch_run",
            "chhs_batch_step", "chhs_batch_launch_counts", "chhs_batch_last_error", "chhs_batch_destroy",
-           "chhs_profile_smooth32", "chhs_probe_fp64", "chhs_batch_profile_step", "chhs_set_tuning",
+           "chhs_profile_smooth32", "chhs_probe_fp64", "chhs_probe_l2", "chhs_batch_profile_step", "chhs_set_tuning",
            "chhs_norm_checks", "chhs_batch_set_tuning", "chhs_batch_autotune"]
 
 # kernel kinds of chhs_profile_step
@@ -127,6 +127,7 @@ def lib():
             "chhs_batch_destroy": (None, [_vp]),
             "chhs_profile_smooth32": (i, [_vp, i, _dp]),
             "chhs_probe_fp64": (i, [_dp]),
+            "chhs_probe_l2": (i, [ctypes.c_size_t, i, _dp]),
             "chhs_batch_profile_step": (i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
             "chhs_set_tuning": (i, [_vp, ctypes.c_void_p]),
             "chhs_batch_set_tuning": (i, [_vp, ctypes.c_void_p]),
@@ -564,6 +565,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def probe_l2(nbytes=48 << 20, passes=50):
+    """Measured L2 read bandwidth of the current device in GB/s (a buffer of
+    nbytes read passes times with L1-bypassing loads)."""
+    g = ctypes.c_double(0.0)
+    st = lib().chhs_probe_l2(int(nbytes), int(passes), ctypes.byref(g))
+    if st != CHHS_OK:
+        raise ChhsError(st, "chhs_probe_l2 failed")
+    return g.value
 
 
 def probe_fp64():

@@ -1305,6 +1305,57 @@ chhs_status chhs_probe_fp64(double* tflops_out) {
   return CHHS_OK;
 }
 
+// Read bandwidth of the L2: every thread sums 16-byte words of a buffer that
+// fits in the L2, bypassing L1 (ld.global.cg), for `passes` passes.
+__global__ void k_l2_probe(const float4* buf, long long n4, int passes, float* sink) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float acc = 0.f;
+  for (int p = 0; p < passes; ++p)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const float4 v = __ldcg(buf + i);
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  if (acc == 12345.678f) sink[0] = acc;  // keeps the loads live; the buffer holds zeros
+}
+
+chhs_status chhs_probe_l2(size_t bytes, int passes, double* gbs_out) {
+  chhs_t* run = nullptr;  // no handle: CU reports the status only
+  if (!gbs_out || passes < 1 || bytes < (1u << 20) || bytes > ((size_t)1 << 30)) return CHHS_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0, l2 = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+  if (bytes > (size_t)l2 / 2) return CHHS_ERR_INVALID_ARG;
+  struct Res {
+    float4* buf = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Res() {
+      if (buf) cudaFree(buf);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } r;
+  const long long n4 = (long long)(bytes / sizeof(float4));
+  if (cudaMalloc(&r.buf, (size_t)n4 * sizeof(float4)) != cudaSuccess) {
+    cudaGetLastError();
+    return CHHS_ERR_OOM;
+  }
+  CU(cudaMemset(r.buf, 0, (size_t)n4 * sizeof(float4)));
+  CU(cudaEventCreate(&r.a));
+  CU(cudaEventCreate(&r.b));
+  const int blocks = nsm * 8, threads = 256;
+  k_l2_probe<<<blocks, threads>>>(r.buf, n4, 2, nullptr);  // brings the buffer into the L2
+  CU(cudaEventRecord(r.a));
+  k_l2_probe<<<blocks, threads>>>(r.buf, n4, passes, nullptr);
+  CU(cudaEventRecord(r.b));
+  CU(cudaEventSynchronize(r.b));
+  CU(cudaGetLastError());
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, r.a, r.b));
+  *gbs_out = (double)n4 * sizeof(float4) * passes / (ms * 1e-3) / 1e9;
+  return CHHS_OK;
+}
+
 chhs_status chhs_set_tuning(chhs_t* run, const chhs_tuning* t) {
   if (!run || !t) return fail(run, CHHS_ERR_INVALID_ARG, "NULL argument");
   if (run->pending) return fail(run, CHHS_ERR_INVALID_ARG, "steps pending: call chhs_wait first");

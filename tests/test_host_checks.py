@@ -145,7 +145,7 @@ def test_every_handle_entry_point_is_covered():
                    "chhs_energy_noalloc", "chhs_server_create", "chhs_num_levels", "chhs_destroy",
                    "chhs_last_error", "chhs_server_destroy", "chhs_batch_workspace_bytes", "chhs_batch_create",
                    "chhs_batch_size", "chhs_batch_run", "chhs_batch_last_error", "chhs_batch_destroy",
-                   "chhs_probe_fp64"}
+                   "chhs_probe_fp64", "chhs_probe_l2"}
     assert set(chhs.EXPORTS) - handle_free == set(HANDLE_CALLS)
 
 
@@ -264,3 +264,13 @@ def test_batch_arguments_checked_before_any_cuda_call(L):
     assert L.chhs_batch_step(None, 1, None, None, None) == INVALID
     assert L.chhs_batch_size(None) == 0 and L.chhs_batch_run(None, 0) is None
     L.chhs_batch_destroy(None)
+
+
+def test_probe_argument_checks(L):
+    """The measurement probes refuse bad arguments before any CUDA call."""
+    g = ctypes.c_double()
+    assert L.chhs_probe_fp64(None) == INVALID
+    assert L.chhs_probe_l2(1 << 24, 10, None) == INVALID
+    assert L.chhs_probe_l2(1 << 24, 0, ctypes.byref(g)) == INVALID
+    assert L.chhs_probe_l2(1000, 10, ctypes.byref(g)) == INVALID
+    assert L.chhs_probe_l2(1 << 31, 10, ctypes.byref(g)) == INVALID
