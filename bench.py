@@ -66,15 +66,21 @@ L2_PROBE_SOURCE = ("measured: chhs_probe_l2 (48 MiB held in the L2, read 50 time
 
 
 def l2_peak():
-    """Measured L2 read bandwidth (GB/s) of this GPU, best of three probes."""
+    """Measured L2 read bandwidth (GB/s) of this GPU, best of three probes
+    (None if the probe fails: the L2 figures are then left out)."""
     from paper_1611_02967_gb300 import chhs
-    return max(chhs.probe_l2() for _ in range(3))
+    try:
+        return max(chhs.probe_l2() for _ in range(3))
+    except chhs.ChhsError:
+        return None
 
 
 def l2_roofline(alg_bytes, secs, peak, lts_bytes, why):
     """The kernel against the L2's read bandwidth: its algorithmic bytes, and
     the L2 traffic ncu counted for it (lts__t_bytes, when the summary matches
     the source), per launch over its duration."""
+    if not peak:
+        return {"peak_gbs": None, "note": "the L2 probe failed"}
     out = {"peak_gbs": peak, "peak_source": L2_PROBE_SOURCE, "algorithmic_gbs": alg_bytes / secs / 1e9,
            "frac_algorithmic": alg_bytes / secs / 1e9 / peak, "traffic": lts_bytes, "note": why}
     if lts_bytes:
