@@ -77,8 +77,9 @@ def l2_peak():
 
 def l2_roofline(alg_bytes, secs, peak, lts_bytes, why):
     """The kernel against the L2's read bandwidth: its algorithmic bytes, and
-    the L2 traffic ncu counted for it (lts__t_bytes, when the summary matches
-    the source), per launch over its duration."""
+    the L1<->L2 request bytes ncu counted for it (l1tex__m_xbar2l1tex_read_bytes
+    + l1tex__m_l1tex2xbar_write_bytes, when the summary matches the source;
+    the quantity the probe measures), per launch over its duration."""
     if not peak:
         return {"peak_gbs": None, "note": "the L2 probe failed"}
     out = {"peak_gbs": peak, "peak_source": L2_PROBE_SOURCE, "algorithmic_gbs": alg_bytes / secs / 1e9,
@@ -101,6 +102,7 @@ KERNEL_SRC = os.path.join(ROOT, "paper_1611_02967_gb300", "csrc", "chhs_kernels.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_smooth_spinodal512.txt")
 KERNEL_SRC_3D = os.path.join(ROOT, "paper_1611_02967_gb300", "csrc", "chhs_corr3.cuh")
 TRAFFIC_FILE_3D = os.path.join(ROOT, "profiles", "k_smooth_c_bubbles128.txt")
+TRAFFIC_FILE_256 = os.path.join(ROOT, "profiles", "k_smooth_c4_bubbles256.txt")
 
 
 def parse_args(argv=None):
@@ -121,7 +123,7 @@ def parse_args(argv=None):
 
 
 PROFILE_RUNS = ["spinodal512-f64", "spinodal512-mixed", "bubbles128-f64", "bubbles128-mixed",
-                "spinodal64-f64", "spinodal64-mixed"]
+                "spinodal64-f64", "spinodal64-mixed", "bubbles256-mixed"]
 
 
 def profile_run(args):
@@ -489,13 +491,44 @@ def bubbles_leg(stream, flush, steps=10, warmup=3):
                 "achieved": alg / t / 1e9, "peak": gbs, "unit": "GB/s", "frac": alg / t / 1e9 / gbs,
                 "peak_source": src, "traffic": measured_traffic(TRAFFIC_FILE_3D, KERNEL_SRC_3D),
                 "l2": l2_roofline(alg, t, l2_peak(), measured_traffic(TRAFFIC_FILE_3D, KERNEL_SRC_3D,
-                                                                      "lts_bytes_per_launch"),
+                                                                      "l2_request_bytes_per_launch"),
                                   "warm, the level's nine fields (75 MB) largely stay in the L2 between passes"),
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": 1e6 * t,
                 "duration_source": "100 launches back to back between CUDA events (chhs_profile_smooth32)",
                 "note": "24 B per cell per colour launch: the twelve 4-byte values of a sweep (read correction, "
-                        "right-hand sides, phi^m, phi*, phi_b; write the correction) split over its two launches"}
+                        "right-hand sides, phi^m, phi*, phi_b; write the correction) split over its two launches",
+                "grid_256": pass_256(stream)}
         run.close()
+    return out
+
+
+def pass_256(stream, npasses=50):
+    """The same finest-level colour pass on the 256^3 bubbles grid (the
+    largest 3D grid of the serving configuration, h 0.05), whose level fields
+    (~600 MB) do not fit in the L2: back to back, against the byte model and
+    the HBM peak."""
+    from paper_1611_02967_gb300 import chhs, inputs
+    w = inputs.workload("bubbles256")
+    ncell = 256 ** 3
+    run = chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"], stream=stream.cuda_stream,
+                   opts=chhs.default_opts(precision=1))
+    try:
+        run.set_phi(w["phi0"])
+        run.step(1)
+        t = run.profile_smooth32(npasses) / 1e3
+    finally:
+        run.close()
+    alg = SMOOTH_BYTES_F32_PER_CELL_PER_COLOUR * ncell
+    gbs, src = hbm_peak()
+    traffic = measured_traffic(TRAFFIC_FILE_256, KERNEL_SRC_3D)
+    out = {"workload": "3D bubbles 256^3 on (0,12.8)^3, eps 0.04, gamma 2, dt 0.005, 8 tanh bubbles (seed 3), "
+                       "after one step", "achieved": alg / t / 1e9, "peak": gbs, "unit": "GB/s",
+           "frac": alg / t / 1e9 / gbs, "peak_source": src, "algorithmic_bytes_per_launch": alg,
+           "traffic": traffic, "avg_launch_us": 1e6 * t,
+           "duration_source": "%d launches back to back between CUDA events (chhs_profile_smooth32)" % npasses}
+    if traffic:  # the DRAM bytes ncu counted per launch, over the same duration
+        out["traffic_gbs"] = traffic / t / 1e9
+        out["traffic_frac"] = traffic / t / 1e9 / gbs
     return out
 
 
@@ -635,7 +668,7 @@ def run_ours(args):
                         "peak_gbs": hbm_gbs, "peak_source": hbm_src, "frac": hbm_bytes / avg_s / 1e9 / hbm_gbs,
                         "note": "72 B per cell updated (read phi, mu, p, phi^m, phi*, f_mu; write phi, mu, p), "
                                 "the hot-path table's byte model; this kernel is bound by the FP64 pipe"},
-                "l2": l2_roofline(hbm_bytes, avg_s, l2_gbs, measured_traffic(key="lts_bytes_per_launch"),
+                "l2": l2_roofline(hbm_bytes, avg_s, l2_gbs, measured_traffic(key="l2_request_bytes_per_launch"),
                                   "the 512^2 hierarchy (~55 MB) stays in the L2 between passes"),
                 "traffic": traffic, "flop_per_launch": flops_per_launch,
                 "avg_launch_us": 1e6 * avg_s, "avg_launch_us_eager": 1e3 * sm_ms / sm_launch,

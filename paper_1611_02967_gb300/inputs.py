@@ -93,4 +93,8 @@ def workload(name):
         L = 6.4
         return dict(shape=(128, 128, 128), h=L / 128, eps=0.04, gamma=2.0, dt=0.005, steps=100,
                     phi0=bubbles(128, L, 0.04, seed=3))
+    if name == "bubbles256":  # the largest 3D grid of the serving configuration, same h
+        L = 12.8
+        return dict(shape=(256, 256, 256), h=L / 256, eps=0.04, gamma=2.0, dt=0.005, steps=10,
+                    phi0=bubbles(256, L, 0.04, seed=3))
     raise KeyError(name)
