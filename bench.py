@@ -123,7 +123,7 @@ def parse_args(argv=None):
 
 
 PROFILE_RUNS = ["spinodal512-f64", "spinodal512-mixed", "bubbles128-f64", "bubbles128-mixed",
-                "spinodal64-f64", "spinodal64-mixed", "bubbles256-mixed"]
+                "spinodal64-f64", "spinodal64-mixed", "bubbles256-mixed", "batched-mixed"]
 
 
 def profile_run(args):
@@ -134,6 +134,8 @@ def profile_run(args):
 
     from paper_1611_02967_gb300 import chhs, inputs
     name, form = args.profile_run.rsplit("-", 1)
+    if name == "batched":
+        return profile_batched(args)
     w = inputs.workload(name)
     run = chhs.Run(w["shape"], w["h"], w["eps"], w["gamma"], w["dt"],
                    opts=chhs.default_opts(precision=1 if form == "mixed" else 0))
@@ -151,6 +153,31 @@ def profile_run(args):
                                       "us_per_launch": 1e3 * v[0] / v[1] if v[1] else None}
                                   for k, v in prof.items()}}), flush=True)
     run.close()
+    return 0
+
+
+def profile_batched(args):
+    """The batched configuration (256 runs, mixed form, default tuning): W
+    steps through the batch's graph, then K steps launched kernel by kernel
+    (chhs_batch_profile_step); prints the per-kind times."""
+    import torch
+
+    from paper_1611_02967_gb300 import chhs
+    runs, phis, sizes = batched_runs()
+    with chhs.Batch(runs) as b:
+        for k in range(len(runs)):
+            b.runs[k].set_phi(phis[k])
+        if args.warmup:
+            b.step(args.warmup)
+        prof = None
+        for _ in range(args.steps):
+            prof = b.profile_step(prof)
+        torch.cuda.synchronize()
+    total = sum(v[0] for v in prof.values())
+    print(json.dumps({"profile_run": args.profile_run, "steps": args.steps, "ms_per_step": total / args.steps,
+                      "kernels": {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / total,
+                                      "launches_per_step": v[1] / args.steps} for k, v in prof.items()}}),
+          flush=True)
     return 0
 
 
