@@ -453,15 +453,16 @@ struct Enqueue {
     auto pass = [&](int colour, int with_rhs, int pro, const Level<double>& U) {
       if constexpr (DIM == 3) {
         if (quad_level(run, L)) {
-          const int qb = (int)(((long long)(L.nx / 4) * L.ny * L.nz + kSmoothBlock - 1) / kSmoothBlock);
+          const dim3 qg = quad_grid(L.nx, L.ny, L.nz);
+          const int tl = quad_tile(L.nx);
           if (with_rhs)
-            pdl(k_smooth_c4<1, 0>, qb, kSmoothBlock, s, L, C, K, colour, U);
+            pdl_grid(k_smooth_c4<1, 0>, qg, kSmoothBlock, 0, s, L, C, K, colour, U, tl);
           else if (pro == 1)
-            pdl(k_smooth_c4<0, 1>, qb, kSmoothBlock, s, L, C, K, colour, U);
+            pdl_grid(k_smooth_c4<0, 1>, qg, kSmoothBlock, 0, s, L, C, K, colour, U, tl);
           else if (pro == 2)
-            pdl(k_smooth_c4<0, 2>, qb, kSmoothBlock, s, L, C, K, colour, U);
+            pdl_grid(k_smooth_c4<0, 2>, qg, kSmoothBlock, 0, s, L, C, K, colour, U, tl);
           else
-            pdl(k_smooth_c4<0, 0>, qb, kSmoothBlock, s, L, C, K, colour, U);
+            pdl_grid(k_smooth_c4<0, 0>, qg, kSmoothBlock, 0, s, L, C, K, colour, U, tl);
           return;
         }
       }
@@ -494,7 +495,9 @@ struct Enqueue {
 
   // A 3D single-precision level whose colour passes run as x-quads.
   static bool quad_level(const chhs_t* run, const Level<float>& L) {
-    return DIM == 3 && run->quad_passes && L.nx % 4 == 0;
+    if (DIM != 3 || !run->quad_passes || L.nx % 4 != 0) return false;
+    const dim3 g = quad_grid(L.nx, L.ny, L.nz);
+    return g.y <= 65535 && g.z <= 65535;
   }
 
   // Mixed form whose finest level is not in the tail: the last smoothing
@@ -1244,9 +1247,9 @@ chhs_status chhs_profile_smooth32(chhs_t* run, int npasses, double* ms_per_launc
   const dim3 grid((L.nx + tw - 1) / tw, (L.ny + th - 1) / th);
   for (int k = 0; k <= npasses; ++k) {
     if (k == 1) CU(cudaEventRecord(ev.a, run->stream));
-    if (run->dim == 3 && run->quad_passes && L.nx % 4 == 0)
-      pdl(k_smooth_c4<0, 0>, (int)(((long long)(L.nx / 4) * L.ny * L.nz + kSmoothBlock - 1) / kSmoothBlock),
-          kSmoothBlock, run->stream, L, C, K, k & 1, Level<double>{});
+    if (run->dim == 3 && Enqueue<3>::quad_level(run, L))
+      pdl_grid(k_smooth_c4<0, 0>, quad_grid(L.nx, L.ny, L.nz), kSmoothBlock, 0, run->stream, L, C, K, k & 1,
+               Level<double>{}, quad_tile(L.nx));
     else if (run->dim == 3)
       pdl(k_smooth_c<3>, blocks, kSmoothBlock, run->stream, L, C, K, k & 1, 0, 0, Level<double>{});
     else

@@ -325,20 +325,16 @@ __device__ __forceinline__ void prolong_quad(Quad& X, const float* cn, const flo
 // cells only (as pro); U: as in smooth_c_body, here for all four cells of
 // the quad (the other colour's two are final since the previous pass).
 template <int RHS, int PRO>
-__device__ __forceinline__ void smooth_c4_body(int bx, const Level<float>& L, const Level<float>& C,
-                                               const Coefs<float>& K, int colour, const Level<double>& U) {
+__device__ __forceinline__ void smooth_c4_body(const Level<float>& L, const Level<float>& C, const Coefs<float>& K,
+                                               int colour, const Level<double>& U, int tile) {
+  // the block's brick of quads: 2^lq quads in x, 2^ly rows, 2^lz planes
   const int nq = L.nx >> 2;
-  const int t = bx * blockDim.x + threadIdx.x;
-  int row, k;
-  if (t < (1 << 21)) {
-    row = small_div(t, 2.f * L.rhw);  // 2 rn(1/(nx/2)) = rn(1/nq) exactly
-    k = small_div(row, L.rny);
-  } else {
-    row = t / nq;
-    k = row / L.ny;
-  }
-  if (k >= L.nz) return;
-  const int j = row - k * L.ny, q = t - row * nq;
+  const int lq = tile & 15, ly = (tile >> 4) & 15, lz = tile >> 8;
+  const int q = ((int)blockIdx.x << lq) + (threadIdx.x & ((1 << lq) - 1));
+  const int j = ((int)blockIdx.y << ly) + ((threadIdx.x >> lq) & ((1 << ly) - 1));
+  const int k = ((int)blockIdx.z << lz) + (threadIdx.x >> (lq + ly));
+  if (q >= nq || j >= L.ny || k >= L.nz) return;
+  const int row = j + L.ny * k;
   QuadAt Q;
   Q.s = (j + k + colour) & 1;
   Q.sy = L.nx;
@@ -462,15 +458,34 @@ __device__ __forceinline__ void smooth_c4_body(int bx, const Level<float>& L, co
   }
 }
 
-// Launched with (nx/4) ny nz threads.  The plain pass fits 80 registers
+// Bricks of quads per block (kSmoothBlock = 2^7 threads): 2^lq quads in x with
+// 2^lq the smallest power of two >= nx/4 up to 32, and the remaining factor
+// split between y and z (z the smaller), packed as lq | ly << 4 | lz << 8,
+// so that the warps of a block read each other's y and z neighbour rows
+// (L1 hits) instead of rows of other blocks.
+__host__ __device__ inline int quad_tile(int nx) {
+  const int nq = nx / 4;
+  int lq = 0;
+  while ((1 << lq) < nq && lq < 5) ++lq;
+  const int rem = 7 - lq, lz = rem >> 1;
+  return lq | (rem - lz) << 4 | lz << 8;
+}
+__host__ __device__ inline dim3 quad_grid(int nx, int ny, int nz) {
+  const int t = quad_tile(nx), lq = t & 15, ly = (t >> 4) & 15, lz = t >> 8;
+  return dim3((unsigned)((nx / 4 + (1 << lq) - 1) >> lq), (unsigned)((ny + (1 << ly) - 1) >> ly),
+              (unsigned)((nz + (1 << lz) - 1) >> lz));
+}
+
+// Launched on quad_grid with kSmoothBlock threads.  The plain pass fits 80 registers
 // without spills (6 blocks of 128 threads per SM); the passes that also read
 // the coarse level or R u, 128 (4 blocks).
 template <int RHS, int PRO>
 __global__ void __launch_bounds__(kSmoothBlock, (RHS || PRO) ? 4 : 6) k_smooth_c4(const __grid_constant__ Level<float> L,
                                                             const __grid_constant__ Level<float> C, Coefs<float> K,
-                                                            int colour, const __grid_constant__ Level<double> U) {
+                                                            int colour, const __grid_constant__ Level<double> U,
+                                                            int tile) {
   pdl_enter();
-  smooth_c4_body<RHS, PRO>(blockIdx.x, L, C, K, colour, U);
+  smooth_c4_body<RHS, PRO>(L, C, K, colour, U, tile);
 }
 
 // ---------------------------------------------------------------- restriction

@@ -72,29 +72,31 @@ def test_f64_to_f32_rz_bits():
     assert emu(1e-40) == 0.0 and emu(3.0) == 3.0
 
 
+def _quad_tile(nx):
+    """quad_tile in chhs_corr3.cuh restated: (lq, ly, lz) of a block's brick."""
+    nq = nx // 4
+    lq = 0
+    while (1 << lq) < nq and lq < 5:
+        lq += 1
+    rem = 7 - lq
+    lz = rem >> 1
+    return lq, rem - lz, lz
+
+
 def _quad_pass_accesses(nx, ny, nz, block=128):
     """Every thread of a k_smooth_c4 launch on an nx x ny x nz level (nx a
-    multiple of 4), with the kernel's index arithmetic restated: the quad
-    each live thread takes and every index it loads or stores, on the level
-    and on the next coarser one (nx/2 x ny/2 x nz/2)."""
+    multiple of 4), with the kernel's index arithmetic restated: the grid of
+    bricks (quad_grid), the quad each live thread takes."""
+    lq, ly, lz = _quad_tile(nx)
+    assert (1 << (lq + ly + lz)) == block
     nq = nx // 4
-    threads = nq * ny * nz
-    t = np.arange(-(-threads // block) * block, dtype=np.int64)
-    hw = nx // 2
-    rd = np.float32(2.0) * (np.float32(1.0) / np.float32(hw))  # 2 rn(1/hw)
-    rny = np.float32(1.0) / np.float32(ny)
-    small = t < (1 << 21)
-
-    def sdiv(a, r):
-        return np.trunc((a.astype(np.float32) + np.float32(0.5)) * r).astype(np.int64)
-
-    row = np.where(small, sdiv(t, rd), t // nq)
-    k = np.where(small, sdiv(row, rny), row // ny)
-    live = k < nz
-    t, row, k = t[live], row[live], k[live]
-    j = row - k * ny
-    q = t - row * nq
-    return t, q, j, k
+    gx, gy, gz = -(-nq // (1 << lq)), -(-ny // (1 << ly)), -(-nz // (1 << lz))
+    bx, by, bz, tid = np.meshgrid(np.arange(gx), np.arange(gy), np.arange(gz), np.arange(block), indexing="ij")
+    q = (bx << lq) + (tid & ((1 << lq) - 1))
+    j = (by << ly) + ((tid >> lq) & ((1 << ly) - 1))
+    k = (bz << lz) + (tid >> (lq + ly))
+    live = (q < nq) & (j < ny) & (k < nz)
+    return None, q[live].ravel(), j[live].ravel(), k[live].ravel()
 
 
 @pytest.mark.parametrize("shape", [(128, 128, 128), (64, 64, 64), (32, 32, 32), (16, 16, 16), (8, 8, 8),
@@ -102,16 +104,19 @@ def _quad_pass_accesses(nx, ny, nz, block=128):
                                    (20, 40, 8)])
 def test_quad_pass_index_map(shape):
     """k_smooth_c4's thread-to-quad map and bounds: each quad of the level is
-    taken by exactly one live thread (the division-free quotient with
-    2 rn(1/(nx/2)) = rn(1/(nx/4)) is exact below 2^21 threads, plain division
-    above), every 16-byte vector starts at a multiple of 4 cells and lies in
+    taken by exactly one live thread of the grid of bricks (blocks of 128
+    threads over 2^lq quads x 2^ly rows x 2^lz planes; the grid's y and z
+    extents within the launch limit for these shapes), every 16-byte vector
+    starts at a multiple of 4 cells and lies in
     the level, the outside x neighbour and the y/z neighbour quads are read
     only where they exist, and the coarse pairs of the prolongation lie in
     the coarser level and start at an even cell."""
     nx, ny, nz = shape
     assert nx % 4 == 0
-    t, q, j, k = _quad_pass_accesses(nx, ny, nz)
+    _, q, j, k = _quad_pass_accesses(nx, ny, nz)
     nq = nx // 4
+    lq, ly, lz = _quad_tile(nx)
+    assert -(-ny // (1 << ly)) <= 65535 and -(-nz // (1 << lz)) <= 65535
     assert np.array_equal(np.sort(q + nq * (j + ny * k)), np.arange(nq * ny * nz))
     assert q.min() >= 0 and q.max() < nq and j.min() >= 0 and j.max() < ny
     ncell = nx * ny * nz
