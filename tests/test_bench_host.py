@@ -72,3 +72,24 @@ def test_committed_profile_names_a_hash_and_bytes():
                 vals[k.strip()] = v.strip()
     assert len(vals["kernel_source_sha256_16"]) == 16
     assert float(vals["dram_bytes_per_launch"]) > 0
+
+
+def test_l2_roofline_fields():
+    # algorithmic and request bytes per launch over the duration, against the probe's bandwidth
+    r = bench.l2_roofline(1e7, 1e-5, 2e4, 2e7, "why")
+    assert r["algorithmic_gbs"] == pytest.approx(1000.0) and r["frac_algorithmic"] == pytest.approx(0.05)
+    assert r["achieved_gbs"] == pytest.approx(2000.0) and r["frac"] == pytest.approx(0.1)
+    assert r["traffic"] == 2e7 and r["note"] == "why"
+    # no request bytes recorded: no achieved figure; no probe: no fractions at all
+    assert "achieved_gbs" not in bench.l2_roofline(1e7, 1e-5, 2e4, None, "why")
+    assert bench.l2_roofline(1e7, 1e-5, None, 2e7, "why")["peak_gbs"] is None
+
+
+def test_committed_3d_profiles_match_the_3d_source():
+    # the 3D pass's summaries were taken on the current colour-pass source and name their bytes
+    src = bench.KERNEL_SRC_3D
+    assert bench.measured_traffic(bench.TRAFFIC_FILE_3D, src) > 0
+    assert bench.measured_traffic(bench.TRAFFIC_FILE_3D, src, "l2_request_bytes_per_launch") > 0
+    assert bench.measured_traffic(bench.TRAFFIC_FILE_256, src) > 0
+    assert bench.measured_traffic(key="l2_request_bytes_per_launch") > 0
+    assert bench.measured_traffic(bench.TRAFFIC_FILE_3D, src, "no_such_key") is None
