@@ -153,3 +153,12 @@ def test_quad_pass_index_map(shape):
             ce = rows[0] + np.where(s == 1, 2, -1)
             assert ((ce[xin] >= 0) & (ce[xin] < cn)).all()
             assert (ce[xin] // cx == rows[0][xin] // cx).all()
+
+
+def test_quad_pass_index_map_random_shapes():
+    """The same checks on seeded random level shapes (x extents multiples of 4
+    up to 512, y and z up to 96, even or odd)."""
+    rng = np.random.default_rng(19)
+    for _ in range(40):
+        shape = (4 * int(rng.integers(1, 129)), int(rng.integers(1, 97)), int(rng.integers(1, 97)))
+        test_quad_pass_index_map(shape)
