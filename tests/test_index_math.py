@@ -162,3 +162,33 @@ def test_quad_pass_index_map_random_shapes():
     for _ in range(40):
         shape = (4 * int(rng.integers(1, 129)), int(rng.integers(1, 97)), int(rng.integers(1, 97)))
         test_quad_pass_index_map(shape)
+
+
+def test_quad_component_selection():
+    """The selections of k_smooth_c4's cell updates (at, xm, xp, put in
+    smooth_c4_cells) restated: for the pass's two cells 4q+s+2h of a quad,
+    `at` picks the cell's own component, xm and xp the components (or the
+    outside neighbour e) at x - 1 and x + 1, and `put` writes the own one."""
+    comps = "xyzw"
+
+    def at(h, s):
+        return ("w" if s else "z") if h else ("y" if s else "x")
+
+    def xm(h, s):
+        return ("z" if s else "y") if h else ("x" if s else "e")
+
+    def xp(h, s):
+        return ("e" if s else "w") if h else ("z" if s else "y")
+
+    for s in (0, 1):
+        e_off = 4 if s else -1  # the outside neighbour: 4q+4 when s = 1, 4q-1 when s = 0
+        for h in (0, 1):
+            own = s + 2 * h  # offset of the updated cell within the quad
+            off = lambda c: e_off if c == "e" else comps.index(c)  # noqa: E731
+            assert off(at(h, s)) == own
+            assert off(xm(h, s)) == own - 1
+            assert off(xp(h, s)) == own + 1
+            # the missing-face rule: e falls back to the quad's end cell, which is
+            # then the updated cell itself (4q when s = 0, 4q+3 when s = 1)
+            if "e" in (xm(h, s), xp(h, s)):
+                assert own == (3 if s else 0)
